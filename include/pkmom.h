@@ -1,0 +1,195 @@
+/*
+ * pkmom - GPU estimator of the power spectra of the discrete cosmic momentum
+ * field with the FFT (Pan, arXiv:2005.06170), for NVIDIA GB300 (sm_103a).
+ *
+ * The estimator (paper Secs. 2 and 3):
+ *   1. moments of the catalogue: total mass, bulk flow v_b, the velocity tensors
+ *      behind the shot noise (Eqs. rawppnoise, rawPtheta, thetanoise);
+ *   2. assignment of the mass density and the three mass-weighted momentum
+ *      components to four periodic grids with the third-order Battle-Lemarie
+ *      (BL) scaling function (Sec. 2.4.1, Eq. rawFFTed);
+ *   3. a 3D real-to-complex FFT of each grid (Sec. 2.4.1);
+ *   4. per Fourier mode, removal of the shot noise times sum_J W^2(k + 2 k_N J)
+ *      and division by the window W^2(k) (Eqs. psn, rawPp, rawPtheta, rawPx),
+ *      then averages in |k| shells of P_deltadelta, P_pp = <|p|^2>,
+ *      P_thetatheta = theta_scale^2 <|k.p|^2> and Re P_deltatheta, with and
+ *      without the bulk flow (Sec. 3: p' = p - (1 + delta) v_b).
+ *
+ * Conventions
+ *   - Positions are in [0, L) or anywhere (wrapped periodically); the grid
+ *     coordinate is u = x * (ng / L), formed in the catalogue's precision.
+ *   - Grid layout: four real grids back to back, each ng x ng x (ng + 2) in C
+ *     order (x slowest, z fastest; the z rows padded by two elements for the
+ *     in-place R2C transform). After pkmom_fft each grid holds its half spectrum,
+ *     ng x ng x (ng/2 + 1) complex values, in place. Grid 0 is the mass density,
+ *     grids 1..3 the momentum components m v_x, m v_y, m v_z.
+ *   - The BL kernel phi (B-spline order m) is realised exactly as the order-m
+ *     B-spline assignment followed, in Fourier space, by the periodic factor
+ *     prod_a Sigma_m(k_a dx)^{-1/2}; Sigma_m is the B-spline alias sum.
+ *   - Spectra are in units of volume ((Mpc/h)^3 for L in Mpc/h) times the squared
+ *     unit of the velocities for the momentum spectra; k in 1/(unit of L).
+ *   - theta = i k.p * theta_scale (theta_scale = 1/(H a f) in the paper; 1 gives
+ *     theta = -div p).
+ *
+ * Ownership: every buffer passed in is owned by the caller. A context owns its
+ * cuFFT plans, its cached per-grid tables and, for pkmom_estimate and
+ * pkmom_estimate_host only, the grids and scratch it allocates on first use.
+ * All calls are asynchronous on the given CUDA stream (a cudaStream_t passed as
+ * void*; NULL = legacy default stream) unless stated. Argument errors are
+ * returned synchronously; a device-side error (a non-finite position) is latched
+ * in the context and returned by pkmom_sync or by the next synchronising call.
+ * A context is used from one host thread at a time.
+ */
+#ifndef PKMOM_H
+#define PKMOM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pkmom_ctx pkmom_ctx;
+
+typedef enum {
+    PKMOM_OK = 0,
+    PKMOM_EINVAL = -1,      /* bad argument (shape, null pointer, range) */
+    PKMOM_ENOMEM = -2,      /* device allocation failed */
+    PKMOM_ECUDA = -3,       /* CUDA runtime error */
+    PKMOM_ECUFFT = -4,      /* cuFFT error */
+    PKMOM_ETIMEOUT = -5,    /* reserved: a bounded device wait gave up */
+    PKMOM_EUNSUPPORTED = -6,/* valid request this build does not support */
+    PKMOM_ESCRATCH = -7,    /* scratch buffer smaller than pkmom_assign_scratch_bytes */
+    PKMOM_EDATA = -8        /* the catalogue held non-finite or out-of-range positions */
+} pkmom_status;
+
+enum { PKMOM_F32 = 0, PKMOM_F64 = 1 };
+
+/* Rows of the output array: out[row * nbins + bin]. */
+enum {
+    PKMOM_ROW_K = 0,        /* mode-weighted mean |k| of the shell */
+    PKMOM_ROW_NMODES = 1,   /* number of Fourier modes (full sphere count) */
+    PKMOM_ROW_PDD = 2,      /* density auto spectrum, shot noise V/N removed */
+    PKMOM_ROW_PPP = 3,      /* momentum P_p (Eq. rawPp), shot noise V sigma_v^2/N removed */
+    PKMOM_ROW_PTT = 4,      /* momentum divergence P_theta (Eq. rawPtheta) */
+    PKMOM_ROW_PDT = 5,      /* Re P_delta-theta (Eq. rawPx), no shot noise in the real part */
+    PKMOM_ROW_PPP_B = 6,    /* P_p' with the bulk flow removed (Sec. 3.1) */
+    PKMOM_ROW_PTT_B = 7,    /* P_theta' (Sec. 3.2) */
+    PKMOM_ROW_PDT_B = 8,    /* Re P_delta-theta' */
+    PKMOM_ROW_SNDD = 9,     /* the subtracted shot noise, shell mean of SN/W^2 */
+    PKMOM_ROW_SNPP = 10,
+    PKMOM_ROW_SNTT = 11,
+    PKMOM_ROW_SNPP_B = 12,
+    PKMOM_ROW_SNTT_B = 13,
+    PKMOM_NROWS = 14
+};
+
+/* A particle catalogue. x,y,z,vx,vy,vz are element pointers with a common stride
+ * in elements (1 for separate arrays, 3 for interleaved (n,3) position and
+ * velocity arrays). mass may be NULL (unit masses). dtype is PKMOM_F32 or
+ * PKMOM_F64 and must equal the precision in pkmom_params. Device pointers for
+ * every call except pkmom_estimate_host (host pointers there). */
+typedef struct {
+    int64_t n;
+    const void *x, *y, *z, *vx, *vy, *vz;
+    const void *mass;
+    int64_t stride;
+    int dtype;
+} pkmom_catalog;
+
+/* What to estimate. Zero-initialise and fill; pkmom_params_default sets the
+ * paper's choices. */
+typedef struct {
+    double box_L;            /* side of the periodic box (> 0) */
+    int ng;                  /* grid points per side: even, 16..2048 */
+    int order;               /* B-spline order m of the BL kernel: 1..4 (4 = BL3, default) */
+    int precision;           /* PKMOM_F32 (FP32 grids and FFT) or PKMOM_F64 */
+    int nbins;               /* number of linear |k| shells, 1..1024 */
+    double kmin_kf;          /* shell range in units of k_f = 2 pi / L; kmin_kf <= 0 means 1 */
+    double kmax_kf;          /* kmax_kf <= 0 means ng/2 (Nyquist); must be <= ng/2 */
+    double theta_scale;      /* theta = i k.p * theta_scale; 1/(H a f) in the paper */
+    int subtract_shot_noise; /* 1: remove the shot noise (default), 0: raw / W^2 */
+    int bulk;                /* 1: also the bulk-flow-subtracted spectra (rows 6-8, 12-13) */
+    int theta_sn_mode;       /* 0: exact per-mode k.Q.k noise (default), 1: isotropic sigma^2/3 */
+} pkmom_params;
+
+/* Catalogue moments written by pkmom_assign (device memory, 16 doubles):
+ * M = sum m, S2 = sum m^2, sum m v (3), R = sum m^2 v (3),
+ * Q = sum m^2 v v^T (xx, yy, zz, xy, xz, yz), n, and one spare. FP64. */
+typedef struct {
+    double M, S2, mv[3], R[3], Q[6], n, spare;
+} pkmom_moments;
+
+void pkmom_params_default(pkmom_params *p, double box_L, int ng, int nbins);
+
+/* Create a context on CUDA device `device` (made current for the calling thread). */
+pkmom_status pkmom_create(pkmom_ctx **ctx, int device);
+pkmom_status pkmom_destroy(pkmom_ctx *ctx);
+const char *pkmom_strerror(pkmom_status s);
+/* Text of the last error seen by this context (never NULL). */
+const char *pkmom_last_error(const pkmom_ctx *ctx);
+
+/* Bytes of the four padded grids for (ng, precision). */
+size_t pkmom_grid_bytes(int ng, int precision);
+/* Bytes of scratch pkmom_assign needs for n particles with these params. */
+size_t pkmom_assign_scratch_bytes(const pkmom_params *p, int64_t n);
+/* Device bytes pkmom_estimate holds for a request (grids + scratch + plan
+ * workspace estimate + staging of the catalogue for pkmom_estimate_host). */
+size_t pkmom_footprint_bytes(const pkmom_params *p, int64_t n);
+
+/* Steps 1-2 (Secs. 2.1-2.2, 2.4.1): moments of the catalogue into *moments_dev
+ * (a device pkmom_moments) and the B-spline assignment of (m, m v) onto the four
+ * grids at `grids` (pkmom_grid_bytes bytes, device; every real element is
+ * written, the two padding elements of each row are not). `scratch` is device
+ * memory of at least pkmom_assign_scratch_bytes bytes (else PKMOM_ESCRATCH). */
+pkmom_status pkmom_assign(pkmom_ctx *ctx, const pkmom_catalog *cat, const pkmom_params *p,
+                          void *grids, void *moments_dev, void *scratch, size_t scratch_bytes,
+                          void *stream);
+
+/* Step 3 (Sec. 2.4.1): in-place 3D R2C FFT (e^{-ikx}, unnormalised) of the four
+ * grids. The first call for a given (ng, precision) creates and caches a cuFFT
+ * plan (this allocates; call once before any stream capture). */
+pkmom_status pkmom_fft(pkmom_ctx *ctx, const pkmom_params *p, void *grids, void *stream);
+
+/* Step 4 (Eqs. psn, rawPp, rawPtheta, rawPx, bfpp, bfpdpx): shell-averaged
+ * spectra from the transformed grids and the moments, into out_dev (device,
+ * PKMOM_NROWS * nbins doubles, layout out[row * nbins + bin]). Empty shells give
+ * NaN. The first call for a given (ng, order, nbins, range) builds and caches
+ * the per-shell mode tables (allocates; call once before any stream capture). */
+pkmom_status pkmom_spectra(pkmom_ctx *ctx, const pkmom_params *p, const void *grids,
+                           const void *moments_dev, double *out_dev, void *stream);
+
+/* Steps 1-4 on a device catalogue, with grids and scratch owned by the context
+ * (allocated on first use and grown when needed). out_dev as for pkmom_spectra. */
+pkmom_status pkmom_estimate(pkmom_ctx *ctx, const pkmom_catalog *cat, const pkmom_params *p,
+                            double *out_dev, void *stream);
+
+/* Steps 1-4 on a HOST catalogue: copies the arrays to context-owned device
+ * memory (cudaMemcpyAsync; pinned host memory makes the copies asynchronous and
+ * fast), runs pkmom_estimate and copies the PKMOM_NROWS * nbins result to the
+ * host array out_host. Synchronises the stream before returning. */
+pkmom_status pkmom_estimate_host(pkmom_ctx *ctx, const pkmom_catalog *cat_host, const pkmom_params *p,
+                                 double *out_host, void *stream);
+
+/* Wait for the stream and return any latched device-side error (PKMOM_EDATA). */
+pkmom_status pkmom_sync(pkmom_ctx *ctx, void *stream);
+
+/* Per-stage timing with CUDA events recorded on the launching stream. When on,
+ * every pkmom_assign/fft/spectra call records start/stop events around each
+ * stage; pkmom_timing_read synchronises on the last events and returns the
+ * accumulated milliseconds and call counts per stage, then resets them.
+ * Stages: 0 moments+histogram, 1 scan, 2 scatter (sort), 3 deposit, 4 FFT,
+ * 5 deconvolution+binning, 6 finalize. */
+enum { PKMOM_STAGE_HIST = 0, PKMOM_STAGE_SCAN, PKMOM_STAGE_SCATTER, PKMOM_STAGE_DEPOSIT,
+       PKMOM_STAGE_FFT, PKMOM_STAGE_BIN, PKMOM_STAGE_FINAL, PKMOM_NSTAGES };
+pkmom_status pkmom_timing_enable(pkmom_ctx *ctx, int on);
+pkmom_status pkmom_timing_read(pkmom_ctx *ctx, double ms[PKMOM_NSTAGES], int64_t calls[PKMOM_NSTAGES]);
+
+/* Number of kernels this context has launched (its own kernels; cuFFT's not counted). */
+int64_t pkmom_kernel_launches(const pkmom_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PKMOM_H */

@@ -1,0 +1,600 @@
+// Steps 1-2 of the estimator on the GPU: catalogue moments and the B-spline
+// assignment of mass and momentum to four periodic grids (paper Secs. 2.1-2.2,
+// Eq. rawFFTed; the BL kernel's Fourier factor is applied in spectra.cu).
+//
+// Pipeline (all on one stream):
+//   k_hist_moments  one pass over the catalogue: FP64 moments (block partials) and a
+//                   histogram of sort keys (key = x-row, y-row, z-segment of the cell);
+//                   each particle keeps the rank its atomic increment returned.
+//   k_moments_final fixed-order sum of the block partials -> pkmom_moments.
+//   k_scan_*        exclusive scan of the key counts -> segment offsets.
+//   k_scatter       writes each particle as a 32-byte record (grid coordinates and the
+//                   four deposited values) at offset[key] + rank: a counting sort.
+//   k_deposit       one CTA per output tile of grid nodes: gathers the particles of
+//                   every segment whose stencils reach the tile (tile + halo, located
+//                   through the offsets), accumulates B-spline weights x values in
+//                   shared memory, then writes each node of the tile exactly once.
+//                   No global atomics, no zero-fill pass.
+#include <cfloat>
+
+#include "pkmom_internal.cuh"
+
+namespace pkmom {
+namespace {
+
+constexpr int kHistThreads = 256;
+constexpr int kGroup = 16;  // particles summed in the catalogue precision before each FP64 add
+
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// floor(u) wrapped into [0, ng); false for non-finite or huge |u|.
+template <typename T>
+__device__ __forceinline__ bool cell_of(T u, int ng, int &c)
+{
+    if (!(fabs(u) < T(1 << 30))) return false;
+    int ic = static_cast<int>(floor(u)) % ng;
+    c = ic < 0 ? ic + ng : ic;
+    return true;
+}
+
+__device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+template <typename T>
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kHistThreads)
+k_hist_moments(const T *__restrict__ x, const T *__restrict__ y, const T *__restrict__ z,
+               const T *__restrict__ vx, const T *__restrict__ vy, const T *__restrict__ vz,
+               const T *__restrict__ mass, int64_t stride, int64_t n, T scale, int ng, int sshift,
+               uint32_t *__restrict__ counts, uint32_t *__restrict__ ranks, double *__restrict__ partials,
+               int *__restrict__ err)
+{
+    const int nseg = ng >> sshift;
+    double acc[kMomentVals];
+    T grp[kMomentVals];
+#pragma unroll
+    for (int k = 0; k < kMomentVals; ++k) acc[k] = 0.0, grp[k] = T(0);
+    int gcount = 0;
+    const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += step) {
+        const int64_t j = i * stride;
+        const T u0 = mul_rn(x[j], scale), u1 = mul_rn(y[j], scale), u2 = mul_rn(z[j], scale);
+        int c0, c1, c2;
+        const bool ok = cell_of(u0, ng, c0) & cell_of(u1, ng, c1) & cell_of(u2, ng, c2);
+        uint32_t rank = 0xffffffffu;
+        if (ok) {
+            const int64_t key = (static_cast<int64_t>(c0) * ng + c1) * nseg + (c2 >> sshift);
+            rank = atomicAdd(counts + key, 1u);
+        } else {
+            *err = 1;
+        }
+        ranks[i] = rank;
+        const T m = mass ? mass[i] : T(1);
+        const T v0 = vx[j], v1 = vy[j], v2 = vz[j];
+        const T m2 = m * m;
+        grp[0] += m;
+        grp[1] += m2;
+        grp[2] += m * v0;
+        grp[3] += m * v1;
+        grp[4] += m * v2;
+        grp[5] += m2 * v0;
+        grp[6] += m2 * v1;
+        grp[7] += m2 * v2;
+        grp[8] += m2 * v0 * v0;
+        grp[9] += m2 * v1 * v1;
+        grp[10] += m2 * v2 * v2;
+        grp[11] += m2 * v0 * v1;
+        grp[12] += m2 * v0 * v2;
+        grp[13] += m2 * v1 * v2;
+        if (++gcount == kGroup) {
+#pragma unroll
+            for (int k = 0; k < kMomentVals; ++k) acc[k] += static_cast<double>(grp[k]), grp[k] = T(0);
+            gcount = 0;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kMomentVals; ++k) acc[k] += static_cast<double>(grp[k]);
+
+    __shared__ double s_part[kHistThreads / 32][kMomentVals];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kMomentVals; ++k) {
+        const double v = warp_sum<T>(acc[k]);
+        if (lane == 0) s_part[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kMomentVals) {
+        double s = 0.0;
+        for (int w = 0; w < kHistThreads / 32; ++w) s += s_part[w][threadIdx.x];
+        partials[static_cast<int64_t>(blockIdx.x) * kMomentWords + threadIdx.x] = s;
+    }
+}
+
+__global__ void k_moments_final(const double *__restrict__ partials, int nblocks, int64_t n_particles,
+                                double *__restrict__ out)
+{
+    // one warp per moment value, fixed summation order
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (k >= kMomentVals) return;
+    double s = 0.0;
+    for (int b = lane; b < nblocks; b += 32) s += partials[static_cast<int64_t>(b) * kMomentWords + k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) out[k] = s;
+    if (k == 0 && lane == 0) {
+        out[kMomentVals] = static_cast<double>(n_particles);
+        out[kMomentVals + 1] = 0.0;
+    }
+}
+
+// ------------------------------------------------------------------ scan
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;  // keys per block
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t &total)
+{
+    __shared__ uint32_t s_w[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < nw ? s_w[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        s_w[lane] = w;  // inclusive prefix of warp totals
+    }
+    __syncthreads();
+    const uint32_t warp_base = warp ? s_w[warp - 1] : 0u;
+    total = s_w[nw - 1];
+    __syncthreads();
+    return warp_base + inc - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_reduce(const uint32_t *__restrict__ counts, int64_t nkeys, uint32_t *__restrict__ blocksums)
+{
+    const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile + static_cast<int64_t>(threadIdx.x) * kScanItems;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < nkeys) s += counts[base + k];
+    uint32_t total;
+    block_exclusive_scan(s, total);
+    if (threadIdx.x == 0) blocksums[blockIdx.x] = total;
+}
+
+// One block: exclusive scan of the block sums in place; writes the grand total
+// to counts[nkeys] (the end offset).
+__global__ void __launch_bounds__(1024)
+k_scan_top(uint32_t *__restrict__ blocksums, int64_t nblocks, uint32_t *__restrict__ counts, int64_t nkeys)
+{
+    const int64_t per = (nblocks + blockDim.x - 1) / blockDim.x;
+    const int64_t b0 = static_cast<int64_t>(threadIdx.x) * per;
+    uint32_t s = 0;
+    for (int64_t k = 0; k < per; ++k)
+        if (b0 + k < nblocks) s += blocksums[b0 + k];
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(s, total);
+    for (int64_t k = 0; k < per; ++k)
+        if (b0 + k < nblocks) {
+            const uint32_t v = blocksums[b0 + k];
+            blocksums[b0 + k] = run;
+            run += v;
+        }
+    if (threadIdx.x == 0) counts[nkeys] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_apply(uint32_t *__restrict__ counts, int64_t nkeys, const uint32_t *__restrict__ blocksums)
+{
+    const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile + static_cast<int64_t>(threadIdx.x) * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < nkeys ? counts[base + k] : 0u;
+        s += v[k];
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(s, total) + blocksums[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < nkeys) {
+            counts[base + k] = run;
+            run += v[k];
+        }
+}
+
+// ------------------------------------------------------------------ scatter
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_scatter(const T *__restrict__ x, const T *__restrict__ y, const T *__restrict__ z, const T *__restrict__ vx,
+          const T *__restrict__ vy, const T *__restrict__ vz, const T *__restrict__ mass, int64_t stride, int64_t n,
+          T scale, int ng, int sshift, const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ ranks,
+          Record<T> *__restrict__ rec)
+{
+    const int nseg = ng >> sshift;
+    const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += step) {
+        const uint32_t rank = ranks[i];
+        if (rank == 0xffffffffu) continue;
+        const int64_t j = i * stride;
+        const T u0 = mul_rn(x[j], scale), u1 = mul_rn(y[j], scale), u2 = mul_rn(z[j], scale);
+        int c0, c1, c2;
+        cell_of(u0, ng, c0);
+        cell_of(u1, ng, c1);
+        cell_of(u2, ng, c2);
+        const int64_t key = (static_cast<int64_t>(c0) * ng + c1) * nseg + (c2 >> sshift);
+        const uint32_t dst = offsets[key] + rank;
+        const T m = mass ? mass[i] : T(1);
+        Record<T> r;
+        r.u = Vec4<T>{u0, u1, u2, T(0)};
+        r.q = Vec4<T>{m, m * vx[j], m * vy[j], m * vz[j]};
+        rec[dst] = r;
+    }
+}
+
+// ------------------------------------------------------------------ deposit
+// B-spline weights of order M for a particle at fractional offset t = u - floor(u)
+// in its cell; `first` receives the first node relative to floor(u).
+template <int M, typename T>
+__device__ __forceinline__ void bspline_weights(T t, T (&w)[M], int &first)
+{
+    if constexpr (M == 4) {
+        const T s = T(1) - t, t2 = t * t, t3 = t2 * t;
+        const T sixth = T(1) / T(6);
+        w[0] = s * s * s * sixth;
+        w[1] = (T(3) * t3 - T(6) * t2 + T(4)) * sixth;
+        w[2] = (T(-3) * t3 + T(3) * t2 + T(3) * t + T(1)) * sixth;
+        w[3] = t3 * sixth;
+        first = -1;
+    } else if constexpr (M == 3) {
+        const bool up = t >= T(0.5);
+        const T d = up ? t - T(1) : t;  // offset from the nearest node, in [-1/2, 1/2)
+        const T a = T(0.5) - d, b = T(0.5) + d;
+        w[0] = T(0.5) * a * a;
+        w[1] = T(0.75) - d * d;
+        w[2] = T(0.5) * b * b;
+        first = up ? 0 : -1;
+    } else if constexpr (M == 2) {
+        w[0] = T(1) - t;
+        w[1] = t;
+        first = 0;
+    } else {
+        w[0] = T(1);
+        first = t >= T(0.5) ? 1 : 0;
+    }
+}
+
+template <typename T, int M, int T0, int T1, int T2, int NT>
+struct DepositCfg {
+    static constexpr int HL = (M % 2 == 0) ? M / 2 : (M + 1) / 2;  // cells below the tile that reach it
+    static constexpr int HR = (M % 2 == 0) ? M / 2 - 1 : (M - 1) / 2;
+    static constexpr int R0 = T0 + HL + HR, R1 = T1 + HL + HR;
+    static constexpr int MAXR = 2 * R0 * R1;  // up to two particle ranges per row
+    static constexpr int TN = T0 * T1 * T2;
+    static constexpr int IPT = (MAXR + NT - 1) / NT;
+    static constexpr size_t smem = 4 * TN * sizeof(T);
+};
+
+template <typename T, int M, int T0, int T1, int T2, int NT>
+__global__ void __launch_bounds__(NT)
+k_deposit(const Record<T> *__restrict__ rec, const uint32_t *__restrict__ offsets, int ng, int sshift,
+          T *__restrict__ grids, int64_t grid_elems)
+{
+    using C = DepositCfg<T, M, T0, T1, T2, NT>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *acc = reinterpret_cast<T *>(smem_raw);  // [4][T0][T1][T2]
+    __shared__ uint32_t s_beg[C::MAXR];
+    __shared__ uint32_t s_pre[C::MAXR + 1];
+
+    const int ntz = ng / T2, nty = ng / T1;
+    int tile = blockIdx.x;
+    const int tz = tile % ntz;
+    tile /= ntz;
+    const int ty = tile % nty;
+    const int tx = tile / nty;
+    const int t0 = tx * T0, t1 = ty * T1, t2 = tz * T2;
+
+    for (int k = threadIdx.x; k < 4 * C::TN; k += NT) acc[k] = T(0);
+
+    // particle ranges: every (x, y) row within reach, the z segments within reach
+    const int S = 1 << sshift;
+    const int nseg = ng >> sshift;
+    const int r0n = C::R0 < ng ? C::R0 : ng;
+    const int r1n = C::R1 < ng ? C::R1 : ng;
+    const int nrows = r0n * r1n;
+    const int zc = (T2 + C::HL + C::HR) < ng ? (T2 + C::HL + C::HR) : ng;
+    int slo = 0, shi = nseg - 1;
+    bool whole = zc == ng;
+    if (!whole) {
+        slo = floordiv(t2 - C::HL, S);
+        shi = floordiv(t2 - C::HL + zc - 1, S);
+        whole = shi - slo + 1 >= nseg;
+        if (whole) slo = 0, shi = nseg - 1;
+    }
+    uint32_t lens[C::IPT];
+    uint32_t my = 0;
+#pragma unroll
+    for (int k = 0; k < C::IPT; ++k) {
+        const int slot = threadIdx.x * C::IPT + k;
+        uint32_t beg = 0, len = 0;
+        if (slot < 2 * nrows) {
+            const int r = slot >> 1, second = slot & 1;
+            int a0 = t0 - C::HL + r / r1n, a1 = t1 - C::HL + r % r1n;
+            a0 = a0 < 0 ? a0 + ng : (a0 >= ng ? a0 - ng : a0);
+            a1 = a1 < 0 ? a1 + ng : (a1 >= ng ? a1 - ng : a1);
+            const int64_t base = (static_cast<int64_t>(a0) * ng + a1) * nseg;
+            int lo = slo, hi = shi;  // segment range of this piece, inclusive
+            bool use = !second;
+            if (slo < 0) {
+                if (second) lo = 0, hi = shi, use = true;
+                else lo = slo + nseg, hi = nseg - 1;
+            } else if (shi >= nseg) {
+                if (second) lo = 0, hi = shi - nseg, use = true;
+                else hi = nseg - 1;
+            }
+            if (use) {
+                beg = offsets[base + lo];
+                len = offsets[base + hi + 1] - beg;
+            }
+        }
+        if (slot < C::MAXR) s_beg[slot] = beg;
+        lens[k] = len;
+        my += len;
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(my, total);
+#pragma unroll
+    for (int k = 0; k < C::IPT; ++k) {
+        const int slot = threadIdx.x * C::IPT + k;
+        if (slot < C::MAXR) s_pre[slot] = run;
+        run += lens[k];
+    }
+    if (threadIdx.x == 0) s_pre[C::MAXR] = total;
+    __syncthreads();
+
+    // each thread takes a contiguous chunk of the concatenated ranges: neighbouring
+    // lanes work far apart in the tile, which keeps shared-memory atomics spread out
+    const uint32_t chunk = (total + NT - 1) / NT;
+    uint32_t p = threadIdx.x * chunk;
+    const uint32_t pend = p + chunk < total ? p + chunk : total;
+    if (p < pend) {
+        // range containing p: last slot with s_pre[slot] <= p
+        int lo = 0, hi = C::MAXR - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_pre[mid] <= p) lo = mid;
+            else hi = mid - 1;
+        }
+        int slot = lo;
+        for (; p < pend; ++p) {
+            while (p >= s_pre[slot + 1]) ++slot;
+            const uint32_t idx = s_beg[slot] + (p - s_pre[slot]);
+            const Record<T> r = rec[idx];
+            const T u[3] = {r.u.x, r.u.y, r.u.z};
+            const int tb[3] = {t0, t1, t2};
+            const int td[3] = {T0, T1, T2};
+            T w[3][M];
+            int li[3][M];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const T f = floor(u[a]);
+                int c = static_cast<int>(f) % ng;
+                c = c < 0 ? c + ng : c;
+                int first;
+                bspline_weights<M, T>(u[a] - f, w[a], first);
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                    int l = c + first + k - tb[a];
+                    l = l < 0 ? l + ng : (l >= ng ? l - ng : l);
+                    li[a][k] = l < td[a] ? l : -1;
+                }
+            }
+#pragma unroll
+            for (int k0 = 0; k0 < M; ++k0) {
+                if (li[0][k0] < 0) continue;
+#pragma unroll
+                for (int k1 = 0; k1 < M; ++k1) {
+                    if (li[1][k1] < 0) continue;
+                    const T w01 = w[0][k0] * w[1][k1];
+                    const int b01 = (li[0][k0] * T1 + li[1][k1]) * T2;
+#pragma unroll
+                    for (int k2 = 0; k2 < M; ++k2) {
+                        if (li[2][k2] < 0) continue;
+                        const T ww = w01 * w[2][k2];
+                        T *a = acc + b01 + li[2][k2];
+                        atomicAdd(a, r.q.x * ww);
+                        atomicAdd(a + C::TN, r.q.y * ww);
+                        atomicAdd(a + 2 * C::TN, r.q.z * ww);
+                        atomicAdd(a + 3 * C::TN, r.q.w * ww);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // every node of the tile written once, coalesced along z
+    for (int k = threadIdx.x; k < C::TN; k += NT) {
+        const int l2 = k % T2, l01 = k / T2;
+        const int l1 = l01 % T1, l0 = l01 / T1;
+        const int64_t gi = (static_cast<int64_t>(t0 + l0) * ng + (t1 + l1)) * (ng + 2) + t2 + l2;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) grids[f * grid_elems + gi] = acc[f * C::TN + k];
+    }
+}
+
+struct TileDesc {
+    int prec;
+    int d[3];
+};
+constexpr TileDesc kTiles[] = {
+    {PKMOM_F32, {16, 16, 16}},  // 0
+    {PKMOM_F32, {16, 16, 32}},  // 1
+    {PKMOM_F32, {8, 8, 32}},    // 2
+    {PKMOM_F32, {8, 8, 8}},     // 3
+    {PKMOM_F64, {8, 8, 16}},    // 4
+    {PKMOM_F64, {16, 16, 16}},  // 5
+    {PKMOM_F64, {8, 8, 8}},     // 6
+};
+
+template <typename T, int M, int T0, int T1, int T2, int NT>
+cudaError_t launch_deposit_t(const AssignPlan &pl, const uint32_t *offsets, const Record<T> *rec, void *grids,
+                             cudaStream_t s)
+{
+    using C = DepositCfg<T, M, T0, T1, T2, NT>;
+    auto kern = k_deposit<T, M, T0, T1, T2, NT>;
+    static int configured_device = -1;  // the attribute is per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (configured_device != dev) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(C::smem));
+        if (e != cudaSuccess) return e;
+        configured_device = dev;
+    }
+    const int ng = pl.ng;
+    const int64_t tiles = static_cast<int64_t>(ng / T0) * (ng / T1) * (ng / T2);
+    const int64_t grid_elems = static_cast<int64_t>(ng) * ng * (ng + 2);
+    kern<<<static_cast<unsigned>(tiles), NT, C::smem, s>>>(rec, offsets, ng, pl.sshift, static_cast<T *>(grids),
+                                                           grid_elems);
+    return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t launch_deposit_m(const AssignPlan &pl, const uint32_t *offsets, const void *rec, void *grids,
+                             cudaStream_t s)
+{
+    const auto *rf = static_cast<const Record<float> *>(rec);
+    const auto *rd = static_cast<const Record<double> *>(rec);
+    switch (pl.tile) {
+    case 0: return launch_deposit_t<float, M, 16, 16, 16, 256>(pl, offsets, rf, grids, s);
+    case 1: return launch_deposit_t<float, M, 16, 16, 32, 512>(pl, offsets, rf, grids, s);
+    case 2: return launch_deposit_t<float, M, 8, 8, 32, 256>(pl, offsets, rf, grids, s);
+    case 3: return launch_deposit_t<float, M, 8, 8, 8, 128>(pl, offsets, rf, grids, s);
+    case 4: return launch_deposit_t<double, M, 8, 8, 16, 256>(pl, offsets, rd, grids, s);
+    case 5: return launch_deposit_t<double, M, 16, 16, 16, 256>(pl, offsets, rd, grids, s);
+    case 6: return launch_deposit_t<double, M, 8, 8, 8, 128>(pl, offsets, rd, grids, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+const T *tp(const void *p) { return static_cast<const T *>(p); }
+
+}  // namespace
+
+int deposit_tile_count() { return static_cast<int>(sizeof(kTiles) / sizeof(kTiles[0])); }
+
+void deposit_tile_shape(int tile, int prec, int dims[3])
+{
+    dims[0] = dims[1] = dims[2] = 0;
+    if (tile < 0 || tile >= deposit_tile_count() || kTiles[tile].prec != prec) return;
+    for (int a = 0; a < 3; ++a) dims[a] = kTiles[tile].d[a];
+}
+
+cudaError_t launch_hist_moments(const pkmom_catalog &cat, const AssignPlan &pl, double box_L, void *scratch,
+                                int *err_flag, cudaStream_t s, LaunchStats &st)
+{
+    char *sc = static_cast<char *>(scratch);
+    auto *counts = reinterpret_cast<uint32_t *>(sc + pl.off_counts);
+    auto *ranks = reinterpret_cast<uint32_t *>(sc + pl.off_ranks);
+    auto *partials = reinterpret_cast<double *>(sc + pl.off_partials);
+    cudaError_t e = cudaMemsetAsync(counts, 0, static_cast<size_t>(pl.nkeys + 1) * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    const double scale = static_cast<double>(pl.ng) / box_L;
+    if (pl.prec == PKMOM_F32) {
+        k_hist_moments<float><<<pl.hist_blocks, kHistThreads, 0, s>>>(
+            tp<float>(cat.x), tp<float>(cat.y), tp<float>(cat.z), tp<float>(cat.vx), tp<float>(cat.vy),
+            tp<float>(cat.vz), tp<float>(cat.mass), cat.stride, cat.n, static_cast<float>(scale), pl.ng, pl.sshift,
+            counts, ranks, partials, err_flag);
+    } else {
+        k_hist_moments<double><<<pl.hist_blocks, kHistThreads, 0, s>>>(
+            tp<double>(cat.x), tp<double>(cat.y), tp<double>(cat.z), tp<double>(cat.vx), tp<double>(cat.vy),
+            tp<double>(cat.vz), tp<double>(cat.mass), cat.stride, cat.n, scale, pl.ng, pl.sshift, counts, ranks,
+            partials, err_flag);
+    }
+    st.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments_final(const AssignPlan &pl, int64_t n, void *scratch, double *moments_dev,
+                                 cudaStream_t s, LaunchStats &st)
+{
+    char *sc = static_cast<char *>(scratch);
+    auto *partials = reinterpret_cast<const double *>(sc + pl.off_partials);
+    k_moments_final<<<1, 32 * kMomentVals, 0, s>>>(partials, pl.hist_blocks, n, moments_dev);
+    st.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const AssignPlan &pl, void *scratch, cudaStream_t s, LaunchStats &st)
+{
+    char *sc = static_cast<char *>(scratch);
+    auto *counts = reinterpret_cast<uint32_t *>(sc + pl.off_counts);
+    auto *bsum = reinterpret_cast<uint32_t *>(sc + pl.off_blocksums);
+    const unsigned nb = static_cast<unsigned>(pl.scan_blocks);
+    k_scan_reduce<<<nb, kScanThreads, 0, s>>>(counts, pl.nkeys, bsum);
+    k_scan_top<<<1, 1024, 0, s>>>(bsum, pl.scan_blocks, counts, pl.nkeys);
+    k_scan_apply<<<nb, kScanThreads, 0, s>>>(counts, pl.nkeys, bsum);
+    st.launches += 3;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const pkmom_catalog &cat, const AssignPlan &pl, double box_L, void *scratch,
+                           cudaStream_t s, LaunchStats &st)
+{
+    char *sc = static_cast<char *>(scratch);
+    auto *offsets = reinterpret_cast<const uint32_t *>(sc + pl.off_counts);
+    auto *ranks = reinterpret_cast<const uint32_t *>(sc + pl.off_ranks);
+    const double scale = static_cast<double>(pl.ng) / box_L;
+    const unsigned blocks = pl.hist_blocks;
+    if (pl.prec == PKMOM_F32) {
+        k_scatter<float><<<blocks, 256, 0, s>>>(tp<float>(cat.x), tp<float>(cat.y), tp<float>(cat.z),
+                                                tp<float>(cat.vx), tp<float>(cat.vy), tp<float>(cat.vz),
+                                                tp<float>(cat.mass), cat.stride, cat.n, static_cast<float>(scale),
+                                                pl.ng, pl.sshift, offsets, ranks,
+                                                reinterpret_cast<Record<float> *>(sc + pl.off_records));
+    } else {
+        k_scatter<double><<<blocks, 256, 0, s>>>(tp<double>(cat.x), tp<double>(cat.y), tp<double>(cat.z),
+                                                 tp<double>(cat.vx), tp<double>(cat.vy), tp<double>(cat.vz),
+                                                 tp<double>(cat.mass), cat.stride, cat.n, scale, pl.ng, pl.sshift,
+                                                 offsets, ranks,
+                                                 reinterpret_cast<Record<double> *>(sc + pl.off_records));
+    }
+    st.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deposit(const AssignPlan &pl, void *scratch, void *grids, cudaStream_t s, LaunchStats &st)
+{
+    char *sc = static_cast<char *>(scratch);
+    auto *offsets = reinterpret_cast<const uint32_t *>(sc + pl.off_counts);
+    const void *rec = sc + pl.off_records;
+    cudaError_t e;
+    switch (pl.order) {
+    case 1: e = launch_deposit_m<1>(pl, offsets, rec, grids, s); break;
+    case 2: e = launch_deposit_m<2>(pl, offsets, rec, grids, s); break;
+    case 3: e = launch_deposit_m<3>(pl, offsets, rec, grids, s); break;
+    case 4: e = launch_deposit_m<4>(pl, offsets, rec, grids, s); break;
+    default: return cudaErrorInvalidValue;
+    }
+    st.launches++;
+    return e;
+}
+
+}  // namespace pkmom

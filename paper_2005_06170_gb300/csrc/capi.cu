@@ -1,0 +1,557 @@
+// The C-ABI of libpkmom (include/pkmom.h): argument checking, the per-call
+// assignment plan (sort-key segment length, deposit tile, scratch layout),
+// cached cuFFT plans and per-grid tables, context-owned buffers for
+// pkmom_estimate / pkmom_estimate_host, stage timing with CUDA events.
+#include <cufft.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pkmom_internal.cuh"
+
+using namespace pkmom;
+
+struct PlanEntry {
+    int ng, prec;
+    cufftHandle h;
+};
+
+struct TimedEvent {
+    int stage;
+    cudaEvent_t a, b;
+};
+
+struct pkmom_ctx {
+    int device = 0;
+    int num_sms = 0;
+    std::string last_error;
+    int *d_err = nullptr;  // device-side data error word
+    LaunchStats st;
+    std::vector<PlanEntry> plans;
+    std::vector<SpectraTables> tables;
+    // buffers owned for pkmom_estimate / pkmom_estimate_host
+    void *grids = nullptr;
+    size_t grids_bytes = 0;
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    double *moments = nullptr;
+    double *out_dev = nullptr;
+    size_t out_bytes = 0;
+    void *staging = nullptr;
+    size_t staging_bytes = 0;
+    // timing
+    bool timing = false;
+    std::vector<TimedEvent> pending;
+    std::vector<cudaEvent_t> pool;
+    double ms[PKMOM_NSTAGES] = {0};
+    int64_t calls[PKMOM_NSTAGES] = {0};
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+pkmom_status fail(pkmom_ctx *ctx, pkmom_status s, const std::string &msg)
+{
+    if (ctx) ctx->last_error = msg;
+    return s;
+}
+
+pkmom_status cuda_fail(pkmom_ctx *ctx, cudaError_t e, const char *where)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(ctx, PKMOM_ENOMEM, std::string(where) + ": " + cudaGetErrorString(e));
+    return fail(ctx, PKMOM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define PK_CUDA(call, where)                                  \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+    } while (0)
+
+cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+double umin_of(const pkmom_params &p) { return p.kmin_kf > 0 ? p.kmin_kf : 1.0; }
+double umax_of(const pkmom_params &p) { return p.kmax_kf > 0 ? p.kmax_kf : 0.5 * p.ng; }
+
+pkmom_status check_params(pkmom_ctx *ctx, const pkmom_params *p)
+{
+    if (!p) return fail(ctx, PKMOM_EINVAL, "params is NULL");
+    if (!(p->box_L > 0) || !std::isfinite(p->box_L)) return fail(ctx, PKMOM_EINVAL, "box_L must be > 0");
+    if (p->ng < 16 || p->ng > 2048 || p->ng % 8) return fail(ctx, PKMOM_EINVAL, "ng must be a multiple of 8 in [16, 2048]");
+    if (p->order < 1 || p->order > 4) return fail(ctx, PKMOM_EINVAL, "order must be 1..4");
+    if (p->precision != PKMOM_F32 && p->precision != PKMOM_F64) return fail(ctx, PKMOM_EINVAL, "bad precision");
+    if (p->nbins < 1 || p->nbins > 1024) return fail(ctx, PKMOM_EINVAL, "nbins must be 1..1024");
+    const double lo = umin_of(*p), hi = umax_of(*p);
+    if (!(hi <= 0.5 * p->ng) || !(lo < hi)) return fail(ctx, PKMOM_EINVAL, "need 0 < kmin_kf < kmax_kf <= ng/2");
+    if (p->theta_sn_mode != 0 && p->theta_sn_mode != 1) return fail(ctx, PKMOM_EINVAL, "theta_sn_mode must be 0 or 1");
+    if (!std::isfinite(p->theta_scale)) return fail(ctx, PKMOM_EINVAL, "theta_scale must be finite");
+    return PKMOM_OK;
+}
+
+pkmom_status check_catalog(pkmom_ctx *ctx, const pkmom_catalog *c, const pkmom_params *p)
+{
+    if (!c) return fail(ctx, PKMOM_EINVAL, "catalog is NULL");
+    if (c->n < 1 || c->n >= (int64_t(1) << 31)) return fail(ctx, PKMOM_EINVAL, "n must be in [1, 2^31)");
+    if (!c->x || !c->y || !c->z || !c->vx || !c->vy || !c->vz) return fail(ctx, PKMOM_EINVAL, "null catalog array");
+    if (c->stride < 1) return fail(ctx, PKMOM_EINVAL, "stride must be >= 1");
+    if (c->dtype != p->precision) return fail(ctx, PKMOM_EINVAL, "catalog dtype must equal params precision");
+    return PKMOM_OK;
+}
+
+// How one assignment is laid out: sort-key segment length, deposit tile and scratch.
+AssignPlan plan_assign(const pkmom_params &p, int64_t n, int num_sms)
+{
+    AssignPlan pl;
+    pl.ng = p.ng;
+    pl.order = p.order;
+    pl.prec = p.precision;
+    const double cells = double(p.ng) * p.ng * p.ng;
+    // deposit tile: the largest listed shape that divides ng, for this precision
+    const int pref32[] = {0, 3};
+    const int pref64[] = {4, 6};
+    const int *pref = p.precision == PKMOM_F32 ? pref32 : pref64;
+    pl.tile = pref[1];
+    for (int k = 0; k < 2; ++k) {
+        int d[3];
+        deposit_tile_shape(pref[k], p.precision, d);
+        if (d[0] && p.ng % d[0] == 0 && p.ng % d[1] == 0 && p.ng % d[2] == 0) {
+            pl.tile = pref[k];
+            break;
+        }
+    }
+    int td[3];
+    deposit_tile_shape(pl.tile, p.precision, td);
+    // z segment per sort key: about one particle per key for sparse catalogues,
+    // never longer than the deposit tile, and few enough keys for 32-bit offsets
+    int sshift = 0;
+    const double ppc = double(n) / cells;
+    while ((1 << (sshift + 1)) <= td[2] && (p.ng % (1 << (sshift + 1))) == 0 &&
+           (ppc * (1 << sshift) < 0.5 || cells / (1 << sshift) > double(1u << 30)))
+        ++sshift;
+    pl.sshift = sshift;
+    pl.nkeys = int64_t(p.ng) * p.ng * (p.ng >> sshift);
+    pl.hist_blocks = num_sms * 8;
+    pl.scan_blocks = (pl.nkeys + 8191) / 8192;
+    const size_t rec = p.precision == PKMOM_F32 ? 32 : 64;
+    size_t off = 0;
+    pl.off_counts = off;
+    off = align_up(off + size_t(pl.nkeys + 1) * 4);
+    pl.off_ranks = off;
+    off = align_up(off + size_t(n) * 4);
+    pl.off_records = off;
+    off = align_up(off + size_t(n) * rec);
+    pl.off_partials = off;
+    off = align_up(off + size_t(pl.hist_blocks) * kMomentWords * 8);
+    pl.off_blocksums = off;
+    off = align_up(off + size_t(pl.scan_blocks + 1) * 4);
+    pl.total = off;
+    return pl;
+}
+
+int device_sms(int device)
+{
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0) v = 152;
+    return v;
+}
+
+cudaEvent_t take_event(pkmom_ctx *ctx)
+{
+    if (!ctx->pool.empty()) {
+        cudaEvent_t e = ctx->pool.back();
+        ctx->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct StageTimer {
+    pkmom_ctx *ctx;
+    int stage;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    StageTimer(pkmom_ctx *c, int stg, cudaStream_t st) : ctx(c), stage(stg), s(st)
+    {
+        if (ctx->timing) {
+            a = take_event(ctx);
+            cudaEventRecord(a, s);
+        }
+    }
+    void stop()
+    {
+        if (ctx->timing && a) {
+            cudaEvent_t b = take_event(ctx);
+            cudaEventRecord(b, s);
+            ctx->pending.push_back({stage, a, b});
+            a = nullptr;
+        }
+    }
+    ~StageTimer() { stop(); }
+};
+
+pkmom_status get_plan(pkmom_ctx *ctx, int ng, int prec, cufftHandle *out)
+{
+    for (auto &e : ctx->plans)
+        if (e.ng == ng && e.prec == prec) {
+            *out = e.h;
+            return PKMOM_OK;
+        }
+    cufftHandle h;
+    int n[3] = {ng, ng, ng};
+    int inembed[3] = {ng, ng, ng + 2};
+    int onembed[3] = {ng, ng, ng / 2 + 1};
+    const int idist = ng * ng * (ng + 2);
+    const int odist = ng * ng * (ng / 2 + 1);
+    cufftResult r = cufftPlanMany(&h, 3, n, inembed, 1, idist, onembed, 1, odist,
+                                  prec == PKMOM_F32 ? CUFFT_R2C : CUFFT_D2Z, 4);
+    if (r != CUFFT_SUCCESS) {
+        char buf[96];
+        std::snprintf(buf, sizeof buf, "cufftPlanMany(ng=%d) failed with code %d", ng, int(r));
+        return fail(ctx, r == CUFFT_ALLOC_FAILED ? PKMOM_ENOMEM : PKMOM_ECUFFT, buf);
+    }
+    ctx->plans.push_back({ng, prec, h});
+    *out = h;
+    return PKMOM_OK;
+}
+
+pkmom_status get_tables(pkmom_ctx *ctx, const pkmom_params &p, cudaStream_t s, const SpectraTables **out)
+{
+    const double lo = umin_of(p), hi = umax_of(p);
+    for (auto &t : ctx->tables)
+        if (t.ng == p.ng && t.order == p.order && t.nbins == p.nbins && t.umin == lo && t.umax == hi &&
+            t.prec == p.precision) {
+            *out = &t;
+            return PKMOM_OK;
+        }
+    SpectraTables t;
+    cudaError_t e = build_spectra_tables(t, p.ng, p.order, p.nbins, lo, hi, p.precision, ctx->num_sms, s, ctx->st);
+    if (e != cudaSuccess) {
+        free_spectra_tables(t);
+        return cuda_fail(ctx, e, "building spectra tables");
+    }
+    ctx->tables.push_back(t);
+    *out = &ctx->tables.back();
+    return PKMOM_OK;
+}
+
+pkmom_status ensure(pkmom_ctx *ctx, void **buf, size_t *have, size_t want, const char *what)
+{
+    if (*have >= want && *buf) return PKMOM_OK;
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    cudaError_t e = cudaMalloc(buf, want);
+    if (e != cudaSuccess) {
+        *buf = nullptr;
+        return cuda_fail(ctx, e, what);
+    }
+    *have = want;
+    return PKMOM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pkmom_params_default(pkmom_params *p, double box_L, int ng, int nbins)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->box_L = box_L;
+    p->ng = ng;
+    p->order = 4;
+    p->precision = PKMOM_F32;
+    p->nbins = nbins;
+    p->kmin_kf = 1.0;
+    p->kmax_kf = 0.5 * ng;
+    p->theta_scale = 1.0;
+    p->subtract_shot_noise = 1;
+    p->bulk = 1;
+    p->theta_sn_mode = 0;
+}
+
+const char *pkmom_strerror(pkmom_status s)
+{
+    switch (s) {
+    case PKMOM_OK: return "ok";
+    case PKMOM_EINVAL: return "invalid argument";
+    case PKMOM_ENOMEM: return "device out of memory";
+    case PKMOM_ECUDA: return "CUDA error";
+    case PKMOM_ECUFFT: return "cuFFT error";
+    case PKMOM_ETIMEOUT: return "device wait timed out";
+    case PKMOM_EUNSUPPORTED: return "unsupported";
+    case PKMOM_ESCRATCH: return "scratch buffer too small";
+    case PKMOM_EDATA: return "non-finite or out-of-range particle positions";
+    }
+    return "unknown status";
+}
+
+const char *pkmom_last_error(const pkmom_ctx *ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+pkmom_status pkmom_create(pkmom_ctx **out, int device)
+{
+    if (!out) return PKMOM_EINVAL;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) return PKMOM_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return PKMOM_ECUDA;
+    auto *ctx = new pkmom_ctx;
+    ctx->device = device;
+    ctx->num_sms = device_sms(device);
+    cudaError_t e = cudaMalloc(&ctx->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        delete ctx;
+        return e == cudaErrorMemoryAllocation ? PKMOM_ENOMEM : PKMOM_ECUDA;
+    }
+    *out = ctx;
+    return PKMOM_OK;
+}
+
+pkmom_status pkmom_destroy(pkmom_ctx *ctx)
+{
+    if (!ctx) return PKMOM_EINVAL;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto &p : ctx->plans) cufftDestroy(p.h);
+    for (auto &t : ctx->tables) free_spectra_tables(t);
+    for (auto &t : ctx->pending) cudaEventDestroy(t.a), cudaEventDestroy(t.b);
+    for (auto e : ctx->pool) cudaEventDestroy(e);
+    cudaFree(ctx->grids);
+    cudaFree(ctx->scratch);
+    cudaFree(ctx->moments);
+    cudaFree(ctx->out_dev);
+    cudaFree(ctx->staging);
+    cudaFree(ctx->d_err);
+    delete ctx;
+    return PKMOM_OK;
+}
+
+size_t pkmom_grid_bytes(int ng, int precision)
+{
+    if (ng <= 0) return 0;
+    return size_t(4) * ng * ng * (ng + 2) * (precision == PKMOM_F64 ? 8 : 4);
+}
+
+size_t pkmom_assign_scratch_bytes(const pkmom_params *p, int64_t n)
+{
+    if (!p || check_params(nullptr, p) != PKMOM_OK || n < 1) return 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return plan_assign(*p, n, device_sms(dev)).total;
+}
+
+size_t pkmom_footprint_bytes(const pkmom_params *p, int64_t n)
+{
+    if (!p || check_params(nullptr, p) != PKMOM_OK || n < 1) return 0;
+    const size_t elem = p->precision == PKMOM_F64 ? 8 : 4;
+    const size_t grids = pkmom_grid_bytes(p->ng, p->precision);
+    const size_t staging = size_t(n) * 7 * elem;
+    // cuFFT's in-place workspace is at most one grid's worth
+    return grids + grids / 4 + pkmom_assign_scratch_bytes(p, n) + staging + (size_t(64) << 10);
+}
+
+pkmom_status pkmom_assign(pkmom_ctx *ctx, const pkmom_catalog *cat, const pkmom_params *p, void *grids,
+                          void *moments_dev, void *scratch, size_t scratch_bytes, void *stream)
+{
+    if (!ctx) return PKMOM_EINVAL;
+    pkmom_status s;
+    if ((s = check_params(ctx, p)) != PKMOM_OK) return s;
+    if ((s = check_catalog(ctx, cat, p)) != PKMOM_OK) return s;
+    if (!grids || !moments_dev || !scratch) return fail(ctx, PKMOM_EINVAL, "null grids, moments or scratch");
+    PK_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const AssignPlan pl = plan_assign(*p, cat->n, ctx->num_sms);
+    if (scratch_bytes < pl.total) return fail(ctx, PKMOM_ESCRATCH, "scratch smaller than pkmom_assign_scratch_bytes");
+    cudaStream_t st = as_stream(stream);
+    {
+        StageTimer t(ctx, PKMOM_STAGE_HIST, st);
+        PK_CUDA(launch_hist_moments(*cat, pl, p->box_L, scratch, ctx->d_err, st, ctx->st), "moments/histogram");
+        PK_CUDA(launch_moments_final(pl, cat->n, scratch, static_cast<double *>(moments_dev), st, ctx->st),
+                "moments");
+    }
+    {
+        StageTimer t(ctx, PKMOM_STAGE_SCAN, st);
+        PK_CUDA(launch_scan(pl, scratch, st, ctx->st), "scan");
+    }
+    {
+        StageTimer t(ctx, PKMOM_STAGE_SCATTER, st);
+        PK_CUDA(launch_scatter(*cat, pl, p->box_L, scratch, st, ctx->st), "scatter");
+    }
+    {
+        StageTimer t(ctx, PKMOM_STAGE_DEPOSIT, st);
+        PK_CUDA(launch_deposit(pl, scratch, grids, st, ctx->st), "deposit");
+    }
+    return PKMOM_OK;
+}
+
+pkmom_status pkmom_fft(pkmom_ctx *ctx, const pkmom_params *p, void *grids, void *stream)
+{
+    if (!ctx) return PKMOM_EINVAL;
+    pkmom_status s;
+    if ((s = check_params(ctx, p)) != PKMOM_OK) return s;
+    if (!grids) return fail(ctx, PKMOM_EINVAL, "null grids");
+    PK_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cufftHandle h;
+    if ((s = get_plan(ctx, p->ng, p->precision, &h)) != PKMOM_OK) return s;
+    cudaStream_t st = as_stream(stream);
+    if (cufftSetStream(h, st) != CUFFT_SUCCESS) return fail(ctx, PKMOM_ECUFFT, "cufftSetStream failed");
+    StageTimer t(ctx, PKMOM_STAGE_FFT, st);
+    cufftResult r;
+    if (p->precision == PKMOM_F32)
+        r = cufftExecR2C(h, static_cast<cufftReal *>(grids), static_cast<cufftComplex *>(grids));
+    else
+        r = cufftExecD2Z(h, static_cast<cufftDoubleReal *>(grids), static_cast<cufftDoubleComplex *>(grids));
+    if (r != CUFFT_SUCCESS) return fail(ctx, PKMOM_ECUFFT, "cufftExec failed with code " + std::to_string(int(r)));
+    return PKMOM_OK;
+}
+
+pkmom_status pkmom_spectra(pkmom_ctx *ctx, const pkmom_params *p, const void *grids, const void *moments_dev,
+                           double *out_dev, void *stream)
+{
+    if (!ctx) return PKMOM_EINVAL;
+    pkmom_status s;
+    if ((s = check_params(ctx, p)) != PKMOM_OK) return s;
+    if (!grids || !moments_dev || !out_dev) return fail(ctx, PKMOM_EINVAL, "null grids, moments or output");
+    PK_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t st = as_stream(stream);
+    const SpectraTables *t = nullptr;
+    if ((s = get_tables(ctx, *p, st, &t)) != PKMOM_OK) return s;
+    {
+        StageTimer tm(ctx, PKMOM_STAGE_BIN, st);
+        PK_CUDA(launch_bin(*t, grids, static_cast<const double *>(moments_dev), st, ctx->st), "binning");
+    }
+    {
+        StageTimer tm(ctx, PKMOM_STAGE_FINAL, st);
+        PK_CUDA(launch_finalize(*t, *p, static_cast<const double *>(moments_dev), out_dev, st, ctx->st), "finalize");
+    }
+    return PKMOM_OK;
+}
+
+pkmom_status pkmom_estimate(pkmom_ctx *ctx, const pkmom_catalog *cat, const pkmom_params *p, double *out_dev,
+                            void *stream)
+{
+    if (!ctx) return PKMOM_EINVAL;
+    pkmom_status s;
+    if ((s = check_params(ctx, p)) != PKMOM_OK) return s;
+    if ((s = check_catalog(ctx, cat, p)) != PKMOM_OK) return s;
+    if (!out_dev) return fail(ctx, PKMOM_EINVAL, "null output");
+    PK_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const AssignPlan pl = plan_assign(*p, cat->n, ctx->num_sms);
+    if ((s = ensure(ctx, &ctx->grids, &ctx->grids_bytes, pkmom_grid_bytes(p->ng, p->precision), "grids")) != PKMOM_OK)
+        return s;
+    if ((s = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, pl.total, "scratch")) != PKMOM_OK) return s;
+    if (!ctx->moments) PK_CUDA(cudaMalloc(reinterpret_cast<void **>(&ctx->moments), kMomentWords * 8), "moments");
+    if ((s = pkmom_assign(ctx, cat, p, ctx->grids, ctx->moments, ctx->scratch, ctx->scratch_bytes, stream)) != PKMOM_OK)
+        return s;
+    if ((s = pkmom_fft(ctx, p, ctx->grids, stream)) != PKMOM_OK) return s;
+    return pkmom_spectra(ctx, p, ctx->grids, ctx->moments, out_dev, stream);
+}
+
+pkmom_status pkmom_estimate_host(pkmom_ctx *ctx, const pkmom_catalog *cat, const pkmom_params *p, double *out_host,
+                                 void *stream)
+{
+    if (!ctx) return PKMOM_EINVAL;
+    pkmom_status s;
+    if ((s = check_params(ctx, p)) != PKMOM_OK) return s;
+    if ((s = check_catalog(ctx, cat, p)) != PKMOM_OK) return s;
+    if (!out_host) return fail(ctx, PKMOM_EINVAL, "null output");
+    PK_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const size_t elem = p->precision == PKMOM_F64 ? 8 : 4;
+    const int64_t n = cat->n;
+    // interleaved (n,3) arrays are copied as one block each; separate arrays one by one
+    const char *bx = static_cast<const char *>(cat->x);
+    const char *bv = static_cast<const char *>(cat->vx);
+    const bool pos_il = cat->stride == 3 && static_cast<const char *>(cat->y) == bx + elem &&
+                        static_cast<const char *>(cat->z) == bx + 2 * elem;
+    const bool vel_il = cat->stride == 3 && static_cast<const char *>(cat->vy) == bv + elem &&
+                        static_cast<const char *>(cat->vz) == bv + 2 * elem;
+    if (cat->stride != 1 && !(pos_il && vel_il))
+        return fail(ctx, PKMOM_EUNSUPPORTED, "host catalogues must be separate arrays or interleaved (n,3) arrays");
+    const size_t block = align_up(size_t(n) * elem);
+    const size_t want = 7 * block;
+    if ((s = ensure(ctx, &ctx->staging, &ctx->staging_bytes, want, "staging")) != PKMOM_OK) return s;
+    const size_t out_bytes = size_t(PKMOM_NROWS) * p->nbins * sizeof(double);
+    if ((s = ensure(ctx, reinterpret_cast<void **>(&ctx->out_dev), &ctx->out_bytes, out_bytes, "output")) != PKMOM_OK)
+        return s;
+    cudaStream_t st = as_stream(stream);
+    char *stg = static_cast<char *>(ctx->staging);
+    pkmom_catalog dcat = *cat;
+    if (cat->stride == 3) {
+        PK_CUDA(cudaMemcpyAsync(stg, cat->x, 3 * size_t(n) * elem, cudaMemcpyHostToDevice, st), "copy positions");
+        PK_CUDA(cudaMemcpyAsync(stg + 3 * block, cat->vx, 3 * size_t(n) * elem, cudaMemcpyHostToDevice, st),
+                "copy velocities");
+        dcat.x = stg, dcat.y = stg + elem, dcat.z = stg + 2 * elem;
+        dcat.vx = stg + 3 * block, dcat.vy = stg + 3 * block + elem, dcat.vz = stg + 3 * block + 2 * elem;
+    } else {
+        const void *src[6] = {cat->x, cat->y, cat->z, cat->vx, cat->vy, cat->vz};
+        const void **dst[6] = {&dcat.x, &dcat.y, &dcat.z, &dcat.vx, &dcat.vy, &dcat.vz};
+        for (int a = 0; a < 6; ++a) {
+            PK_CUDA(cudaMemcpyAsync(stg + a * block, src[a], size_t(n) * elem, cudaMemcpyHostToDevice, st),
+                    "copy catalogue");
+            *dst[a] = stg + a * block;
+        }
+    }
+    if (cat->mass) {
+        PK_CUDA(cudaMemcpyAsync(stg + 6 * block, cat->mass, size_t(n) * elem, cudaMemcpyHostToDevice, st),
+                "copy masses");
+        dcat.mass = stg + 6 * block;
+    }
+    if ((s = pkmom_estimate(ctx, &dcat, p, ctx->out_dev, stream)) != PKMOM_OK) return s;
+    PK_CUDA(cudaMemcpyAsync(out_host, ctx->out_dev, out_bytes, cudaMemcpyDeviceToHost, st), "copy result");
+    return pkmom_sync(ctx, stream);
+}
+
+pkmom_status pkmom_sync(pkmom_ctx *ctx, void *stream)
+{
+    if (!ctx) return PKMOM_EINVAL;
+    PK_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    PK_CUDA(cudaStreamSynchronize(as_stream(stream)), "stream synchronize");
+    int flag = 0;
+    PK_CUDA(cudaMemcpy(&flag, ctx->d_err, sizeof flag, cudaMemcpyDeviceToHost), "read error word");
+    if (flag) {
+        PK_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)), "clear error word");
+        return fail(ctx, PKMOM_EDATA, "catalogue held non-finite or out-of-range positions (|x ng/L| >= 2^30)");
+    }
+    return PKMOM_OK;
+}
+
+pkmom_status pkmom_timing_enable(pkmom_ctx *ctx, int on)
+{
+    if (!ctx) return PKMOM_EINVAL;
+    ctx->timing = on != 0;
+    return PKMOM_OK;
+}
+
+pkmom_status pkmom_timing_read(pkmom_ctx *ctx, double ms[PKMOM_NSTAGES], int64_t calls[PKMOM_NSTAGES])
+{
+    if (!ctx || !ms || !calls) return PKMOM_EINVAL;
+    for (auto &t : ctx->pending) {
+        PK_CUDA(cudaEventSynchronize(t.b), "event synchronize");
+        float v = 0.f;
+        PK_CUDA(cudaEventElapsedTime(&v, t.a, t.b), "event elapsed");
+        ctx->ms[t.stage] += v;
+        ctx->calls[t.stage] += 1;
+        ctx->pool.push_back(t.a);
+        ctx->pool.push_back(t.b);
+    }
+    ctx->pending.clear();
+    for (int k = 0; k < PKMOM_NSTAGES; ++k) {
+        ms[k] = ctx->ms[k];
+        calls[k] = ctx->calls[k];
+        ctx->ms[k] = 0;
+        ctx->calls[k] = 0;
+    }
+    return PKMOM_OK;
+}
+
+int64_t pkmom_kernel_launches(const pkmom_ctx *ctx) { return ctx ? ctx->st.launches : 0; }
+
+}  // extern "C"

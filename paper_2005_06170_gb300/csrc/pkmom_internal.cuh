@@ -1,0 +1,79 @@
+// Internal declarations shared by the CUDA translation units of libpkmom.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pkmom.h"
+
+namespace pkmom {
+
+// Number of doubles in a device pkmom_moments.
+constexpr int kMomentWords = 16;
+// Per-block moment partials: M, S2, mv[3], R[3], Q[6] = 14 values (padded to 16).
+constexpr int kMomentVals = 14;
+// Values accumulated per shell by the binning kernel:
+// 0 |F_d|^2, 1 |F_p|^2, 2 |n.F_p|^2, 3 Im(conj F_d  n.F_p), 4-6 the same three
+// for F_p' = F_p - v_b F_d. Each weighted by mode weight * g(n) = w / prod Bhat^2.
+constexpr int kBinVals = 7;
+// Data-independent per-shell sums: 0 sum w, 1 sum w |n|, 2 sum w h, 3-8 sum w h n_a n_b
+// (xx, yy, zz, xy, xz, yz), h = prod Sigma / prod Bhat^2 = 1 / W^2.
+constexpr int kModeVals = 9;
+
+// One sorted particle: grid coordinates u (3) and the four deposited values
+// (m, m vx, m vy, m vz). 32 bytes in FP32, 64 in FP64.
+template <typename T> struct alignas(4 * sizeof(T)) Vec4 { T x, y, z, w; };
+template <typename T> struct Record { Vec4<T> u; Vec4<T> q; };
+
+// Host-side decisions for one assignment (see plan_assign in capi.cu).
+struct AssignPlan {
+    int ng = 0, order = 4, prec = PKMOM_F32;
+    int sshift = 0;          // z-segment length S = 1 << sshift cells per sort key
+    int64_t nkeys = 0;       // ng * ng * (ng >> sshift)
+    int tile = 0;            // deposit tile id (see deposit launcher)
+    int hist_blocks = 0;     // blocks of the moments+histogram kernel
+    int64_t scan_blocks = 0; // blocks of the key scan
+    size_t off_counts = 0, off_ranks = 0, off_records = 0, off_partials = 0, off_blocksums = 0;
+    size_t total = 0;
+};
+
+struct LaunchStats {
+    int64_t launches = 0;
+};
+
+// ---------------------------------------------------------------- assign.cu
+cudaError_t launch_hist_moments(const pkmom_catalog &cat, const AssignPlan &pl, double box_L, void *scratch,
+                                int *err_flag, cudaStream_t s, LaunchStats &st);
+cudaError_t launch_moments_final(const AssignPlan &pl, int64_t n, void *scratch, double *moments_dev,
+                                 cudaStream_t s, LaunchStats &st);
+cudaError_t launch_scan(const AssignPlan &pl, void *scratch, cudaStream_t s, LaunchStats &st);
+cudaError_t launch_scatter(const pkmom_catalog &cat, const AssignPlan &pl, double box_L, void *scratch,
+                           cudaStream_t s, LaunchStats &st);
+cudaError_t launch_deposit(const AssignPlan &pl, void *scratch, void *grids, cudaStream_t s, LaunchStats &st);
+// Tile shapes the deposit kernel is instantiated for (x, y, z nodes).
+int deposit_tile_count();
+void deposit_tile_shape(int tile, int prec, int dims[3]);
+
+// ---------------------------------------------------------------- spectra.cu
+struct SpectraTables {
+    int ng = 0, order = 0, nbins = 0, prec = -1;
+    double umin = 0, umax = 0;
+    int nsq_max = 0;
+    uint16_t *bintab = nullptr;  // [nsq_max + 1] shell of |n|^2, 0xFFFF outside
+    void *g_full = nullptr;      // [ng] 1/Bhat^2 per full axis (T = float or double)
+    void *g_half = nullptr;      // [ng/2+1]
+    double *h_full = nullptr;    // [ng] Sigma/Bhat^2 (FP64), for the mode tables
+    double *h_half = nullptr;
+    double *mode_sums = nullptr; // [kModeVals][nbins]
+    double *partials = nullptr;  // [bin_blocks][kBinVals][nbins]
+    int bin_blocks = 0;
+};
+cudaError_t build_spectra_tables(SpectraTables &t, int ng, int order, int nbins, double umin, double umax, int prec,
+                                 int num_sms, cudaStream_t s, LaunchStats &st);
+void free_spectra_tables(SpectraTables &t);
+cudaError_t launch_bin(const SpectraTables &t, const void *grids, const double *moments_dev, cudaStream_t s,
+                       LaunchStats &st);
+cudaError_t launch_finalize(const SpectraTables &t, const pkmom_params &p, const double *moments_dev,
+                            double *out, cudaStream_t s, LaunchStats &st);
+
+}  // namespace pkmom

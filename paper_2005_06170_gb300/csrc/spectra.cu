@@ -1,0 +1,460 @@
+// Step 4 of the estimator on the GPU: window deconvolution, shot-noise
+// subtraction and |k|-shell averages of the density, momentum, momentum-
+// divergence and cross spectra, with and without the bulk flow (paper Sec. 2,
+// Eqs. psn, rawPp, rawPtheta, rawPx; Sec. 3, Eqs. bfpp, bfpdpx).
+//
+// Per mode n (integer wave vector, k = k_f n) the four transformed B-spline
+// grids F_d, F_p give the BL-assigned fields times C(n) = prod Sigma_m^{-1/2};
+// dividing by the BL window W = prod Bhat_m Sigma_m^{-1/2} leaves
+//     P_raw / W^2 = g(n) |F|^2,   g = 1 / prod_a Bhat_m(2 pi n_a / ng)^2,
+// and the shot noise times sum_J W^2(k + 2 k_N J) (= 1 for the orthonormal BL
+// function) divided by W^2 is SN * h(n), h = prod Sigma_m / prod Bhat_m^2.
+//
+// k_bin accumulates, per shell, sum w g |F_d|^2, sum w g |F_p|^2,
+// sum w g |n.F_p|^2 and sum w g Im(conj F_d  n.F_p) for F_p and for
+// F_p' = F_p - v_b F_d, with the half-spectrum weight w (1 on the planes n_z = 0
+// and ng/2, else 2). Per-mode values are formed in the grid precision, combined
+// across the lanes of a warp that fall in the same shell, and added into FP64
+// per-CTA shell sums in shared memory; the CTA sums go to a partial array that
+// a fixed-order reduction combines. The data-independent sums (mode counts,
+// sum w |n|, sum w h, sum w h n n^T) are built once per grid/shell layout by
+// k_mode_sums in FP64. k_finalize subtracts the shot noise at the shell level in
+// FP64, where the cancellation against large shot noise is harmless.
+#include <cmath>
+#include <vector>
+
+#include "pkmom_internal.cuh"
+
+namespace pkmom {
+namespace {
+
+template <typename T> struct Cx { T x, y; };
+
+constexpr int kBinThreads = 256;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+// Add the values of the lanes of each run of equal `bin` (runs are contiguous in
+// lane order) and let the first lane of each run add them to s_bins[k * nbins + bin].
+template <int NV, typename V>
+__device__ __forceinline__ void flush_runs(int bin, V (&v)[NV], double *s_bins, int nbins)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int prev = __shfl_up_sync(full, bin, 1);
+    const bool head = lane == 0 || prev != bin;
+    const unsigned heads = __ballot_sync(full, head);
+    const int run = __popc(heads & (full >> (31 - lane)));
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int orun = __shfl_down_sync(full, run, d);
+        const bool take = lane + d < 32 && orun == run;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const V o = __shfl_down_sync(full, v[k], d);
+            if (take) v[k] += o;
+        }
+    }
+    if (head && bin >= 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) atomicAdd(s_bins + k * nbins + bin, static_cast<double>(v[k]));
+    }
+}
+
+// Mode of lane `lane` in chunk `ch` (32 consecutive half-spectrum modes): row and z index.
+__device__ __forceinline__ void chunk_mode(uint32_t ch, int lane, int ng, int nh, int &i0, int &i1, int &l)
+{
+    const uint32_t m0 = ch * 32u;
+    const uint32_t row0 = m0 / static_cast<uint32_t>(nh);
+    int ll = static_cast<int>(m0 - row0 * nh) + lane;
+    int drow = 0;
+    while (ll >= nh) ll -= nh, ++drow;
+    const int r0 = static_cast<int>(row0 / static_cast<uint32_t>(ng));
+    int r1 = static_cast<int>(row0 - static_cast<uint32_t>(r0) * ng) + drow;
+    int rr0 = r0;
+    while (r1 >= ng) r1 -= ng, ++rr0;
+    i0 = rr0;
+    i1 = r1;
+    l = ll;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBinThreads)
+k_bin(const Cx<T> *__restrict__ F, int64_t gstride, int ng, uint32_t nmodes, const uint16_t *__restrict__ bintab,
+      int nsq_max, const T *__restrict__ gf, const T *__restrict__ gh, const double *__restrict__ mom, int nbins,
+      double *__restrict__ partials)
+{
+    extern __shared__ double s_bins[];  // [kBinVals][nbins]
+    for (int k = threadIdx.x; k < kBinVals * nbins; k += blockDim.x) s_bins[k] = 0.0;
+    __syncthreads();
+    const int nh = ng / 2 + 1;
+    const double Mtot = mom[0];
+    const T vb0 = static_cast<T>(mom[2] / Mtot), vb1 = static_cast<T>(mom[3] / Mtot), vb2 = static_cast<T>(mom[4] / Mtot);
+    const int lane = threadIdx.x & 31;
+    const uint32_t nchunks = (nmodes + 31u) / 32u;
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t ch = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ch < nchunks; ch += nwarps) {
+        const uint32_t mode = ch * 32u + lane;
+        int bin = -1;
+        T v[kBinVals];
+#pragma unroll
+        for (int k = 0; k < kBinVals; ++k) v[k] = T(0);
+        if (mode < nmodes) {
+            int i0, i1, l;
+            chunk_mode(ch, lane, ng, nh, i0, i1, l);
+            const int n0 = i0 < ng / 2 ? i0 : i0 - ng;
+            const int n1 = i1 < ng / 2 ? i1 : i1 - ng;
+            const int nsq = n0 * n0 + n1 * n1 + l * l;
+            const int b = nsq <= nsq_max ? static_cast<int>(bintab[nsq]) : 0xffff;
+            if (b != 0xffff) {
+                bin = b;
+                const T g = gf[i0] * gf[i1] * gh[l] * ((l == 0 || l == nh - 1) ? T(1) : T(2));
+                const Cx<T> d = F[mode], p0 = F[gstride + mode], p1 = F[2 * gstride + mode],
+                            p2 = F[3 * gstride + mode];
+                const T fn0 = static_cast<T>(n0), fn1 = static_cast<T>(n1), fn2 = static_cast<T>(l);
+                // n . F_p
+                const T kr = fn0 * p0.x + fn1 * p1.x + fn2 * p2.x;
+                const T ki = fn0 * p0.y + fn1 * p1.y + fn2 * p2.y;
+                const T d2 = d.x * d.x + d.y * d.y;
+                v[0] = g * d2;
+                v[1] = g * (p0.x * p0.x + p0.y * p0.y + p1.x * p1.x + p1.y * p1.y + p2.x * p2.x + p2.y * p2.y);
+                v[2] = g * (kr * kr + ki * ki);
+                v[3] = g * (d.x * ki - d.y * kr);  // Im(conj(F_d) * (n.F_p))
+                // bulk flow removed: F_p' = F_p - v_b F_d
+                const Cx<T> q0{p0.x - vb0 * d.x, p0.y - vb0 * d.y};
+                const Cx<T> q1{p1.x - vb1 * d.x, p1.y - vb1 * d.y};
+                const Cx<T> q2{p2.x - vb2 * d.x, p2.y - vb2 * d.y};
+                const T jr = fn0 * q0.x + fn1 * q1.x + fn2 * q2.x;
+                const T ji = fn0 * q0.y + fn1 * q1.y + fn2 * q2.y;
+                v[4] = g * (q0.x * q0.x + q0.y * q0.y + q1.x * q1.x + q1.y * q1.y + q2.x * q2.x + q2.y * q2.y);
+                v[5] = g * (jr * jr + ji * ji);
+                v[6] = g * (d.x * ji - d.y * jr);
+            }
+        }
+        flush_runs<kBinVals, T>(bin, v, s_bins, nbins);
+    }
+    __syncthreads();
+    double *out = partials + static_cast<int64_t>(blockIdx.x) * kBinVals * nbins;
+    for (int k = threadIdx.x; k < kBinVals * nbins; k += blockDim.x) out[k] = s_bins[k];
+}
+
+__global__ void __launch_bounds__(kBinThreads)
+k_mode_sums(int ng, uint32_t nmodes, const uint16_t *__restrict__ bintab, int nsq_max, const double *__restrict__ hf,
+            const double *__restrict__ hh, int nbins, double *__restrict__ partials)
+{
+    extern __shared__ double s_bins[];  // [kModeVals][nbins]
+    for (int k = threadIdx.x; k < kModeVals * nbins; k += blockDim.x) s_bins[k] = 0.0;
+    __syncthreads();
+    const int nh = ng / 2 + 1;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nchunks = (nmodes + 31u) / 32u;
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t ch = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ch < nchunks; ch += nwarps) {
+        const uint32_t mode = ch * 32u + lane;
+        int bin = -1;
+        double v[kModeVals];
+#pragma unroll
+        for (int k = 0; k < kModeVals; ++k) v[k] = 0.0;
+        if (mode < nmodes) {
+            int i0, i1, l;
+            chunk_mode(ch, lane, ng, nh, i0, i1, l);
+            const int n0 = i0 < ng / 2 ? i0 : i0 - ng;
+            const int n1 = i1 < ng / 2 ? i1 : i1 - ng;
+            const int nsq = n0 * n0 + n1 * n1 + l * l;
+            const int b = nsq <= nsq_max ? static_cast<int>(bintab[nsq]) : 0xffff;
+            if (b != 0xffff) {
+                bin = b;
+                const double w = (l == 0 || l == nh - 1) ? 1.0 : 2.0;
+                const double h = w * hf[i0] * hf[i1] * hh[l];
+                const double a0 = n0, a1 = n1, a2 = l;
+                v[0] = w;
+                v[1] = w * sqrt(static_cast<double>(nsq));
+                v[2] = h;
+                v[3] = h * a0 * a0;
+                v[4] = h * a1 * a1;
+                v[5] = h * a2 * a2;
+                v[6] = h * a0 * a1;
+                v[7] = h * a0 * a2;
+                v[8] = h * a1 * a2;
+            }
+        }
+        flush_runs<kModeVals, double>(bin, v, s_bins, nbins);
+    }
+    __syncthreads();
+    double *out = partials + static_cast<int64_t>(blockIdx.x) * kModeVals * nbins;
+    for (int k = threadIdx.x; k < kModeVals * nbins; k += blockDim.x) out[k] = s_bins[k];
+}
+
+// One block per shell: out[k * nbins + b] = sum_j partials[j][k][b], fixed order.
+template <int NV>
+__global__ void __launch_bounds__(256)
+k_reduce_partials(const double *__restrict__ partials, int nblk, int nbins, double *__restrict__ out)
+{
+    const int b = blockIdx.x;
+    double s[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) s[k] = 0.0;
+    for (int j = threadIdx.x; j < nblk; j += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s[k] += partials[(static_cast<int64_t>(j) * NV + k) * nbins + b];
+    __shared__ double red[NV][256];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < NV) out[threadIdx.x * nbins + b] = red[threadIdx.x][0];
+}
+
+struct FinalParams {
+    double V, kf, ts;
+    int sub, bulk, iso, nbins;
+};
+
+// sum_ab Q_ab H_ab for symmetric Q, H stored as xx, yy, zz, xy, xz, yz
+__device__ __forceinline__ double qdot(const double *Q, const double *H)
+{
+    return Q[0] * H[0] + Q[1] * H[1] + Q[2] * H[2] + 2.0 * (Q[3] * H[3] + Q[4] * H[4] + Q[5] * H[5]);
+}
+
+__global__ void k_finalize(const double *__restrict__ sums /*[kBinVals][nbins]*/,
+                           const double *__restrict__ modes /*[kModeVals][nbins]*/, const double *__restrict__ mom,
+                           FinalParams fp, double *__restrict__ out)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nb = fp.nbins;
+    if (b >= nb) return;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    const double n = modes[b];
+    auto put = [&](int row, double v) { out[row * nb + b] = v; };
+    put(PKMOM_ROW_NMODES, n);
+    if (!(n > 0.0)) {
+        for (int r = 0; r < PKMOM_NROWS; ++r)
+            if (r != PKMOM_ROW_NMODES) put(r, nan);
+        return;
+    }
+    const double M = mom[0], S2 = mom[1];
+    const double vb[3] = {mom[2] / M, mom[3] / M, mom[4] / M};
+    const double R[3] = {mom[5], mom[6], mom[7]};
+    const double *Q = mom + 8;
+    const double H = modes[2 * nb + b];
+    double H2[6];
+    for (int k = 0; k < 6; ++k) H2[k] = modes[(3 + k) * nb + b];
+    const double c = fp.V / (M * M * n);
+    const double ct = c * fp.ts * fp.ts * fp.kf * fp.kf;
+    const double cx = c * fp.ts * fp.kf;
+    const double sub = fp.sub ? 1.0 : 0.0;
+    const double trH2 = H2[0] + H2[1] + H2[2];
+
+    put(PKMOM_ROW_K, fp.kf * modes[nb + b] / n);
+    const double sn_dd = c * S2 * H;
+    put(PKMOM_ROW_PDD, c * sums[0 * nb + b] - sub * sn_dd);
+    put(PKMOM_ROW_SNDD, sn_dd);
+
+    const double trQ = Q[0] + Q[1] + Q[2];
+    const double sn_pp = c * trQ * H;
+    const double sn_tt = ct * (fp.iso ? trQ * trH2 / 3.0 : qdot(Q, H2));
+    put(PKMOM_ROW_PPP, c * sums[1 * nb + b] - sub * sn_pp);
+    put(PKMOM_ROW_PTT, ct * sums[2 * nb + b] - sub * sn_tt);
+    put(PKMOM_ROW_PDT, cx * sums[3 * nb + b]);
+    put(PKMOM_ROW_SNPP, sn_pp);
+    put(PKMOM_ROW_SNTT, sn_tt);
+
+    if (fp.bulk) {
+        // Q' = sum m^2 (v - v_b)(v - v_b)^T = Q - v_b R^T - R v_b^T + v_b v_b^T S2 (Sec. 3.1)
+        const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+        double Qb[6];
+        for (int k = 0; k < 6; ++k)
+            Qb[k] = Q[k] - vb[ia[k]] * R[ib[k]] - R[ia[k]] * vb[ib[k]] + vb[ia[k]] * vb[ib[k]] * S2;
+        const double trQb = Qb[0] + Qb[1] + Qb[2];
+        const double sn_ppb = c * trQb * H;
+        const double sn_ttb = ct * (fp.iso ? trQb * trH2 / 3.0 : qdot(Qb, H2));
+        put(PKMOM_ROW_PPP_B, c * sums[4 * nb + b] - sub * sn_ppb);
+        put(PKMOM_ROW_PTT_B, ct * sums[5 * nb + b] - sub * sn_ttb);
+        put(PKMOM_ROW_PDT_B, cx * sums[6 * nb + b]);
+        put(PKMOM_ROW_SNPP_B, sn_ppb);
+        put(PKMOM_ROW_SNTT_B, sn_ttb);
+    } else {
+        const int rows[5] = {PKMOM_ROW_PPP_B, PKMOM_ROW_PTT_B, PKMOM_ROW_PDT_B, PKMOM_ROW_SNPP_B, PKMOM_ROW_SNTT_B};
+        for (int r = 0; r < 5; ++r) put(rows[r], nan);
+    }
+}
+
+// ---------------------------------------------------------------- host tables
+// B_{2m}(n) at the integers, n = 0..m (textbook values of the centred cardinal
+// B-splines of even order 2, 4, 6, 8), giving Sigma_m(w) = sum_n B_2m(n) cos(n w).
+const double *euler_frobenius(int m)
+{
+    static const double b2[] = {1.0};
+    static const double b4[] = {2.0 / 3.0, 1.0 / 6.0};
+    static const double b6[] = {11.0 / 20.0, 13.0 / 60.0, 1.0 / 120.0};
+    static const double b8[] = {151.0 / 315.0, 397.0 / 1680.0, 1.0 / 42.0, 1.0 / 5040.0};
+    switch (m) {
+    case 1: return b2;
+    case 2: return b4;
+    case 3: return b6;
+    case 4: return b8;
+    default: return nullptr;
+    }
+}
+
+double sigma_m(double w, int m)
+{
+    const double *c = euler_frobenius(m);
+    double s = c[0];
+    for (int n = 1; n < m; ++n) s += 2.0 * c[n] * std::cos(n * w);
+    return s;
+}
+
+double bhat2(double w, int m)
+{
+    const double x = 0.5 * w;
+    const double sx = x == 0.0 ? 1.0 : std::sin(x) / x;
+    double r = 1.0;
+    for (int k = 0; k < m; ++k) r *= sx;
+    return r * r;
+}
+
+template <typename T>
+cudaError_t upload(void **dst, const std::vector<T> &src)
+{
+    cudaError_t e = cudaMalloc(dst, src.size() * sizeof(T));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+}  // namespace
+
+void free_spectra_tables(SpectraTables &t)
+{
+    cudaFree(t.bintab);
+    cudaFree(t.g_full);
+    cudaFree(t.g_half);
+    cudaFree(t.h_full);
+    cudaFree(t.h_half);
+    cudaFree(t.mode_sums);
+    cudaFree(t.partials);
+    t = SpectraTables{};
+}
+
+cudaError_t build_spectra_tables(SpectraTables &t, int ng, int order, int nbins, double umin, double umax, int prec,
+                                 int num_sms, cudaStream_t s, LaunchStats &st)
+{
+    t.ng = ng;
+    t.order = order;
+    t.nbins = nbins;
+    t.umin = umin;
+    t.umax = umax;
+    t.prec = prec;
+    const int nh = ng / 2 + 1;
+    // shells: the same FP64 expression as the definition of the bins
+    t.nsq_max = static_cast<int>(std::floor(umax * umax)) + 1;
+    std::vector<uint16_t> bintab(t.nsq_max + 1, 0xffff);
+    for (int nsq = 1; nsq <= t.nsq_max; ++nsq) {
+        const double u = std::sqrt(static_cast<double>(nsq));
+        if (u < umin || u > umax) continue;
+        double tb = std::floor(((u - umin) * nbins) / (umax - umin));
+        if (tb > nbins - 1) tb = nbins - 1;
+        bintab[nsq] = static_cast<uint16_t>(tb);
+    }
+    std::vector<double> gfd(ng), ghd(nh), hfd(ng), hhd(nh);
+    for (int i = 0; i < ng; ++i) {
+        const int ni = i < ng / 2 ? i : i - ng;
+        const double w = kTwoPi * ni / ng;
+        gfd[i] = 1.0 / bhat2(w, order);
+        hfd[i] = sigma_m(w, order) / bhat2(w, order);
+    }
+    for (int i = 0; i < nh; ++i) {
+        const double w = kTwoPi * i / ng;
+        ghd[i] = 1.0 / bhat2(w, order);
+        hhd[i] = sigma_m(w, order) / bhat2(w, order);
+    }
+    cudaError_t e;
+    if ((e = upload(reinterpret_cast<void **>(&t.bintab), bintab)) != cudaSuccess) return e;
+    if (prec == PKMOM_F32) {
+        std::vector<float> gf(gfd.begin(), gfd.end()), gh(ghd.begin(), ghd.end());
+        if ((e = upload(&t.g_full, gf)) != cudaSuccess) return e;
+        if ((e = upload(&t.g_half, gh)) != cudaSuccess) return e;
+    } else {
+        if ((e = upload(&t.g_full, gfd)) != cudaSuccess) return e;
+        if ((e = upload(&t.g_half, ghd)) != cudaSuccess) return e;
+    }
+    if ((e = upload(reinterpret_cast<void **>(&t.h_full), hfd)) != cudaSuccess) return e;
+    if ((e = upload(reinterpret_cast<void **>(&t.h_half), hhd)) != cudaSuccess) return e;
+
+    const uint32_t nmodes = static_cast<uint32_t>(static_cast<int64_t>(ng) * ng * nh);
+    const uint32_t nchunks = (nmodes + 31u) / 32u;
+    const int warps_per_block = kBinThreads / 32;
+    int64_t want = (nchunks + warps_per_block - 1) / warps_per_block;
+    const int64_t cap = static_cast<int64_t>(num_sms) * 4;
+    t.bin_blocks = static_cast<int>(want < cap ? want : cap);
+    if (t.bin_blocks < 1) t.bin_blocks = 1;
+    if ((e = cudaMalloc(reinterpret_cast<void **>(&t.partials),
+                        static_cast<size_t>(t.bin_blocks) * kModeVals * nbins * sizeof(double))) != cudaSuccess)
+        return e;
+    if ((e = cudaMalloc(reinterpret_cast<void **>(&t.mode_sums), static_cast<size_t>(kModeVals + kBinVals) * nbins *
+                                                                       sizeof(double))) != cudaSuccess)
+        return e;
+    const size_t smem = static_cast<size_t>(kModeVals) * nbins * sizeof(double);
+    if ((e = cudaFuncSetAttribute(k_mode_sums, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem))) !=
+        cudaSuccess)
+        return e;
+    k_mode_sums<<<t.bin_blocks, kBinThreads, smem, s>>>(ng, nmodes, t.bintab, t.nsq_max, t.h_full, t.h_half, nbins,
+                                                        t.partials);
+    k_reduce_partials<kModeVals><<<nbins, 256, 0, s>>>(t.partials, t.bin_blocks, nbins, t.mode_sums);
+    st.launches += 2;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
+cudaError_t launch_bin(const SpectraTables &t, const void *grids, const double *moments_dev, cudaStream_t s,
+                       LaunchStats &st)
+{
+    const int ng = t.ng, nh = ng / 2 + 1;
+    const uint32_t nmodes = static_cast<uint32_t>(static_cast<int64_t>(ng) * ng * nh);
+    const int64_t gstride = static_cast<int64_t>(ng) * ng * nh;  // complex elements per grid
+    const size_t smem = static_cast<size_t>(kBinVals) * t.nbins * sizeof(double);
+    cudaError_t e;
+    if (t.prec == PKMOM_F32) {
+        if ((e = cudaFuncSetAttribute(k_bin<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(smem))) != cudaSuccess)
+            return e;
+        k_bin<float><<<t.bin_blocks, kBinThreads, smem, s>>>(
+            static_cast<const Cx<float> *>(grids), gstride, ng, nmodes, t.bintab, t.nsq_max,
+            static_cast<const float *>(t.g_full), static_cast<const float *>(t.g_half), moments_dev, t.nbins,
+            t.partials);
+    } else {
+        if ((e = cudaFuncSetAttribute(k_bin<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(smem))) != cudaSuccess)
+            return e;
+        k_bin<double><<<t.bin_blocks, kBinThreads, smem, s>>>(
+            static_cast<const Cx<double> *>(grids), gstride, ng, nmodes, t.bintab, t.nsq_max,
+            static_cast<const double *>(t.g_full), static_cast<const double *>(t.g_half), moments_dev, t.nbins,
+            t.partials);
+    }
+    st.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const SpectraTables &t, const pkmom_params &p, const double *moments_dev, double *out,
+                            cudaStream_t s, LaunchStats &st)
+{
+    double *sums = t.mode_sums + static_cast<size_t>(kModeVals) * t.nbins;
+    k_reduce_partials<kBinVals><<<t.nbins, 256, 0, s>>>(t.partials, t.bin_blocks, t.nbins, sums);
+    FinalParams fp;
+    fp.V = p.box_L * p.box_L * p.box_L;
+    fp.kf = kTwoPi / p.box_L;
+    fp.ts = p.theta_scale;
+    fp.sub = p.subtract_shot_noise;
+    fp.bulk = p.bulk;
+    fp.iso = p.theta_sn_mode == 1;
+    fp.nbins = t.nbins;
+    k_finalize<<<(t.nbins + 127) / 128, 128, 0, s>>>(sums, t.mode_sums, moments_dev, fp, out);
+    st.launches += 2;
+    return cudaGetLastError();
+}
+
+}  // namespace pkmom

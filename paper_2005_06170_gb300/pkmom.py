@@ -1,0 +1,261 @@
+"""Python binding of libpkmom (include/pkmom.h): argument marshalling only.
+
+Every step of the estimator runs in the library's CUDA kernels (and cuFFT);
+PyTorch provides device memory and streams. There is no CPU fallback: if the
+library cannot be loaded or built, importing this module raises.
+
+Typical use::
+
+    from paper_2005_06170_gb300 import pkmom
+    ctx = pkmom.Context(0)
+    p = pkmom.params(box_L=1000.0, ng=256, nbins=128)
+    out = ctx.estimate(pos, vel, p)            # pos, vel: (n,3) CUDA tensors
+    P_pp = out[pkmom.ROW["P_pp"]]
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+F32, F64 = 0, 1
+NROWS = 14
+ROW = {"k": 0, "n_modes": 1, "P_dd": 2, "P_pp": 3, "P_tt": 4, "P_dt": 5, "P_pp_b": 6, "P_tt_b": 7,
+       "P_dt_b": 8, "SN_dd": 9, "SN_pp": 10, "SN_tt": 11, "SN_pp_b": 12, "SN_tt_b": 13}
+STAGES = ("hist", "scan", "scatter", "deposit", "fft", "bin", "final")
+STATUS = {0: "PKMOM_OK", -1: "PKMOM_EINVAL", -2: "PKMOM_ENOMEM", -3: "PKMOM_ECUDA", -4: "PKMOM_ECUFFT",
+          -5: "PKMOM_ETIMEOUT", -6: "PKMOM_EUNSUPPORTED", -7: "PKMOM_ESCRATCH", -8: "PKMOM_EDATA"}
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("box_L", ctypes.c_double), ("ng", ctypes.c_int), ("order", ctypes.c_int),
+                ("precision", ctypes.c_int), ("nbins", ctypes.c_int), ("kmin_kf", ctypes.c_double),
+                ("kmax_kf", ctypes.c_double), ("theta_scale", ctypes.c_double),
+                ("subtract_shot_noise", ctypes.c_int), ("bulk", ctypes.c_int), ("theta_sn_mode", ctypes.c_int)]
+
+
+class Catalog(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("vx", ctypes.c_void_p), ("vy", ctypes.c_void_p), ("vz", ctypes.c_void_p),
+                ("mass", ctypes.c_void_p), ("stride", ctypes.c_int64), ("dtype", ctypes.c_int)]
+
+
+class PkmomError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libpkmom.so (building it in-tree with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    L = ctypes.CDLL(path)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    sig = {
+        "pkmom_params_default": (None, [ctypes.POINTER(Params), dbl, i32, i32]),
+        "pkmom_create": (i32, [ctypes.POINTER(vp), i32]),
+        "pkmom_destroy": (i32, [vp]),
+        "pkmom_strerror": (ctypes.c_char_p, [i32]),
+        "pkmom_last_error": (ctypes.c_char_p, [vp]),
+        "pkmom_grid_bytes": (ctypes.c_size_t, [i32, i32]),
+        "pkmom_assign_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(Params), i64]),
+        "pkmom_footprint_bytes": (ctypes.c_size_t, [ctypes.POINTER(Params), i64]),
+        "pkmom_assign": (i32, [vp, ctypes.POINTER(Catalog), ctypes.POINTER(Params), vp, vp, vp, ctypes.c_size_t, vp]),
+        "pkmom_fft": (i32, [vp, ctypes.POINTER(Params), vp, vp]),
+        "pkmom_spectra": (i32, [vp, ctypes.POINTER(Params), vp, vp, vp, vp]),
+        "pkmom_estimate": (i32, [vp, ctypes.POINTER(Catalog), ctypes.POINTER(Params), vp, vp]),
+        "pkmom_estimate_host": (i32, [vp, ctypes.POINTER(Catalog), ctypes.POINTER(Params), vp, vp]),
+        "pkmom_sync": (i32, [vp, vp]),
+        "pkmom_timing_enable": (i32, [vp, i32]),
+        "pkmom_timing_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
+        "pkmom_kernel_launches": (i64, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+EXPORTED = ("pkmom_params_default", "pkmom_create", "pkmom_destroy", "pkmom_strerror", "pkmom_last_error",
+            "pkmom_grid_bytes", "pkmom_assign_scratch_bytes", "pkmom_footprint_bytes", "pkmom_assign",
+            "pkmom_fft", "pkmom_spectra", "pkmom_estimate", "pkmom_estimate_host", "pkmom_sync",
+            "pkmom_timing_enable", "pkmom_timing_read", "pkmom_kernel_launches")
+
+
+def params(box_L: float, ng: int, nbins: int, *, order: int = 4, precision: int = F32, kmin_kf: float = 1.0,
+           kmax_kf: float | None = None, theta_scale: float = 1.0, subtract_shot_noise: bool = True,
+           bulk: bool = True, theta_sn: str = "tensor") -> Params:
+    p = Params()
+    lib().pkmom_params_default(ctypes.byref(p), float(box_L), int(ng), int(nbins))
+    p.order = order
+    p.precision = precision
+    p.kmin_kf = kmin_kf
+    p.kmax_kf = ng / 2 if kmax_kf is None else kmax_kf
+    p.theta_scale = theta_scale
+    p.subtract_shot_noise = int(bool(subtract_shot_noise))
+    p.bulk = int(bool(bulk))
+    p.theta_sn_mode = {"tensor": 0, "isotropic": 1}[theta_sn]
+    return p
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(dtype) -> int:
+    import torch
+    if dtype in (torch.float32, np.float32):
+        return F32
+    if dtype in (torch.float64, np.float64):
+        return F64
+    raise TypeError(f"catalogue arrays must be float32 or float64, not {dtype}")
+
+
+def catalog_from_tensors(pos, vel, mass=None) -> Catalog:
+    """(n,3) contiguous CUDA tensors (and an optional (n,) mass) -> device Catalog."""
+    import torch
+    for t in (pos, vel) + ((mass,) if mass is not None else ()):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("catalogue arrays must be contiguous CUDA tensors")
+    if pos.dim() != 2 or pos.shape[1] != 3 or vel.shape != pos.shape or pos.dtype != vel.dtype:
+        raise ValueError("pos and vel must be (n,3) tensors of the same dtype")
+    es = pos.element_size()
+    c = Catalog()
+    c.n = pos.shape[0]
+    b, v = pos.data_ptr(), vel.data_ptr()
+    c.x, c.y, c.z = b, b + es, b + 2 * es
+    c.vx, c.vy, c.vz = v, v + es, v + 2 * es
+    c.mass = mass.data_ptr() if mass is not None else None
+    c.stride = 3
+    c.dtype = _dtype_code(pos.dtype)
+    return c
+
+
+def catalog_from_numpy(pos: np.ndarray, vel: np.ndarray, mass: np.ndarray | None = None) -> Catalog:
+    """(n,3) C-contiguous host arrays -> host Catalog (for pkmom_estimate_host)."""
+    for a in (pos, vel) + ((mass,) if mass is not None else ()):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host catalogue arrays must be C-contiguous")
+    if pos.ndim != 2 or pos.shape[1] != 3 or vel.shape != pos.shape or pos.dtype != vel.dtype:
+        raise ValueError("pos and vel must be (n,3) arrays of the same dtype")
+    es = pos.itemsize
+    c = Catalog()
+    c.n = pos.shape[0]
+    b, v = pos.ctypes.data, vel.ctypes.data
+    c.x, c.y, c.z = b, b + es, b + 2 * es
+    c.vx, c.vy, c.vz = v, v + es, v + 2 * es
+    c.mass = mass.ctypes.data if mass is not None else None
+    c.stride = 3
+    c.dtype = _dtype_code(pos.dtype.type)
+    return c
+
+
+class Context:
+    """A libpkmom context on one CUDA device (cuFFT plans and tables are cached in it)."""
+
+    def __init__(self, device: int = 0):
+        self._h = ctypes.c_void_p()
+        self._check(lib().pkmom_create(ctypes.byref(self._h), int(device)))
+        self.device = device
+
+    def close(self):
+        if self._h:
+            lib().pkmom_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, status):
+        if status != 0:
+            L = lib()
+            msg = L.pkmom_last_error(self._h).decode() if self._h else L.pkmom_strerror(status).decode()
+            raise PkmomError(status, msg)
+
+    # -- sizes
+    @staticmethod
+    def grid_bytes(ng: int, precision: int = F32) -> int:
+        return lib().pkmom_grid_bytes(ng, precision)
+
+    @staticmethod
+    def scratch_bytes(p: Params, n: int) -> int:
+        return lib().pkmom_assign_scratch_bytes(ctypes.byref(p), n)
+
+    @staticmethod
+    def footprint_bytes(p: Params, n: int) -> int:
+        return lib().pkmom_footprint_bytes(ctypes.byref(p), n)
+
+    # -- the four calls of the C-ABI
+    def assign(self, cat: Catalog, p: Params, grids, moments, scratch, stream=None):
+        self._check(lib().pkmom_assign(self._h, ctypes.byref(cat), ctypes.byref(p), grids.data_ptr(),
+                                       moments.data_ptr(), scratch.data_ptr(), scratch.numel() * scratch.element_size(),
+                                       _stream_ptr(stream)))
+
+    def fft(self, p: Params, grids, stream=None):
+        self._check(lib().pkmom_fft(self._h, ctypes.byref(p), grids.data_ptr(), _stream_ptr(stream)))
+
+    def spectra(self, p: Params, grids, moments, out, stream=None):
+        self._check(lib().pkmom_spectra(self._h, ctypes.byref(p), grids.data_ptr(), moments.data_ptr(),
+                                        out.data_ptr(), _stream_ptr(stream)))
+
+    def estimate(self, pos, vel, p: Params, mass=None, out=None, stream=None):
+        """All steps on device tensors; returns a (NROWS, nbins) float64 CUDA tensor."""
+        import torch
+        cat = catalog_from_tensors(pos, vel, mass)
+        if out is None:
+            out = torch.empty((NROWS, p.nbins), dtype=torch.float64, device=pos.device)
+        self._check(lib().pkmom_estimate(self._h, ctypes.byref(cat), ctypes.byref(p), out.data_ptr(),
+                                         _stream_ptr(stream)))
+        return out
+
+    def estimate_host(self, pos: np.ndarray, vel: np.ndarray, p: Params, mass=None, out=None, stream=None):
+        """All steps on a host catalogue (copied in by the library); returns (NROWS, nbins) numpy."""
+        cat = catalog_from_numpy(pos, vel, mass)
+        if out is None:
+            out = np.empty((NROWS, p.nbins), dtype=np.float64)
+        self._check(lib().pkmom_estimate_host(self._h, ctypes.byref(cat), ctypes.byref(p), out.ctypes.data,
+                                              _stream_ptr(stream)))
+        return out
+
+    def sync(self, stream=None):
+        self._check(lib().pkmom_sync(self._h, _stream_ptr(stream)))
+
+    # -- instrumentation
+    def timing(self, on: bool):
+        self._check(lib().pkmom_timing_enable(self._h, int(bool(on))))
+
+    def timing_read(self) -> dict:
+        ms = (ctypes.c_double * len(STAGES))()
+        calls = (ctypes.c_int64 * len(STAGES))()
+        self._check(lib().pkmom_timing_read(self._h, ms, calls))
+        return {s: (ms[i], calls[i]) for i, s in enumerate(STAGES)}
+
+    def kernel_launches(self) -> int:
+        return int(lib().pkmom_kernel_launches(self._h))
+
+
+def as_dict(out) -> dict:
+    """(NROWS, nbins) array/tensor -> {row name: numpy array}."""
+    a = out.detach().cpu().numpy() if hasattr(out, "detach") else np.asarray(out)
+    return {k: a[i] for k, i in ROW.items()}
+
+
+def library_path() -> str:
+    return os.path.abspath(_build.LIB)
