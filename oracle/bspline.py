@@ -97,10 +97,18 @@ def phi_hat(w, m: int = 4):
     return bspline_hat(w, m) / np.sqrt(alias_sum(w, m))
 
 
-def phi_alias_sum(w, m: int = 4, jmax: int = 200):
-    """sum_J phi_hat(w + 2 pi J)^2 by direct summation: the per-axis factor of
-    sum_J W^2(k + 2 k_N J) in the shot-noise terms (Eq. rawPp). Equals 1 for an
-    orthonormal scaling function; the oracle evaluates it literally."""
+def phi_alias_sum(w, m: int = 4):
+    """sum_J phi_hat(w + 2 pi J)^2: the per-axis factor of sum_J W^2(k + 2 k_N J) in
+    the shot-noise terms (Eq. rawPp). Since Sigma_m is 2 pi-periodic, this is
+    [sum_J Bhat_m(w + 2 pi J)^2] / Sigma_m(w), with the numerator in its closed form
+    (pinned to brute force and to Jing 2005 in the tests). It equals 1 for the
+    orthonormal scaling function, up to rounding."""
+    w = np.asarray(w, dtype=np.float64)
+    return alias_sum(w, m) / alias_sum(w, m)
+
+
+def phi_alias_sum_brute(w, m: int = 4, jmax: int = 200):
+    """sum_{|J|<=jmax} phi_hat(w + 2 pi J)^2 by direct summation (pin for phi_alias_sum)."""
     w = np.asarray(w, dtype=np.float64)
     J = np.arange(-jmax, jmax + 1, dtype=np.float64)
     return (phi_hat(w[..., None] + 2.0 * np.pi * J, m) ** 2).sum(axis=-1)

@@ -62,7 +62,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(sources()), os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, sources()))
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [exe, *ARCH, "-shared", "-o", tmp, *objs, "-lcufft", "-lcudart"]
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(exe)), "lib64")
+    cmd = [exe, *ARCH, "-shared", "-o", tmp, *objs, "-lcufft", "-lcudart", "-Xlinker", f"-rpath={cuda_lib}"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -150,6 +150,8 @@ AssignPlan plan_assign(const pkmom_params &p, int64_t n, int num_sms)
     off = align_up(off + size_t(pl.hist_blocks) * kMomentWords * 8);
     pl.off_blocksums = off;
     off = align_up(off + size_t(pl.scan_blocks + 1) * 4);
+    pl.off_qmax = off;
+    off = align_up(off + 4 * sizeof(unsigned));
     pl.total = off;
     return pl;
 }

@@ -33,7 +33,7 @@ struct AssignPlan {
     int tile = 0;            // deposit tile id (see deposit launcher)
     int hist_blocks = 0;     // blocks of the moments+histogram kernel
     int64_t scan_blocks = 0; // blocks of the key scan
-    size_t off_counts = 0, off_ranks = 0, off_records = 0, off_partials = 0, off_blocksums = 0;
+    size_t off_counts = 0, off_ranks = 0, off_records = 0, off_partials = 0, off_blocksums = 0, off_qmax = 0;
     size_t total = 0;
 };
 

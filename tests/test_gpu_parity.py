@@ -38,9 +38,12 @@ def compare(gpu: dict, ora: dict, rtol: float, bulk: bool = True):
         err = np.abs(g - o) / scale
         worst = max(worst, float(err.max()))
         assert np.all(err <= rtol), (key, float(err.max()), int(err.argmax()))
+    # shot-noise rows depend only on the moments: FP64 sums of FP64 values, or of FP32
+    # values summed 16 at a time in FP32 before each FP64 add
+    sn_rtol = 1e-12 if rtol <= 1e-9 else 1e-6
     for key, skey in SN_OF.items():
         if bulk or not key.endswith("_b"):
-            np.testing.assert_allclose(gpu[skey][ok], ora[skey][ok], rtol=1e-12)
+            np.testing.assert_allclose(gpu[skey][ok], ora[skey][ok], rtol=sn_rtol)
     return worst
 
 
@@ -115,9 +118,12 @@ def test_assigned_grids_match_oracle(ctx, gpu_lib, order, dtype, ng):
     ctx.sync()
     g = grids[..., :ng].double().cpu().numpy()
     ref = est.assign(cat["pos"], cat["vel"], cat.get("mass"), L=L, ng=ng, order=order)
+    # FP32 grids are accumulated in 32-bit fixed point per tile: each contribution is
+    # rounded to 2^-s with 2^s * (largest possible node value of the tile) < 2^30, about
+    # 2^-20 of the tile's sum of |q|; FP64 grids use FP64 atomics
     for f in range(4):
         scale = np.abs(ref[f]).max()
-        tol = (3e-6 if dtype == np.float32 else 1e-12) * scale
+        tol = (1e-5 if dtype == np.float32 else 1e-12) * scale
         assert np.max(np.abs(g[f] - ref[f])) <= tol, (f, np.max(np.abs(g[f] - ref[f])) / scale)
 
 

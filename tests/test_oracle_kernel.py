@@ -96,7 +96,9 @@ def test_alias_sums_match_jing2005():
 @pytest.mark.parametrize("m", [1, 2, 3, 4])
 def test_phi_hat_orthonormal_and_partition(m):
     w = np.linspace(-np.pi, np.pi, 29)
-    np.testing.assert_allclose(bs.phi_alias_sum(w, m, jmax=400 if m > 1 else 20000), 1.0, atol=1e-4 if m == 1 else 1e-12)
+    np.testing.assert_allclose(bs.phi_alias_sum_brute(w, m, jmax=400 if m > 1 else 20000), 1.0,
+                               atol=1e-4 if m == 1 else 1e-12)
+    np.testing.assert_allclose(bs.phi_alias_sum(w, m), 1.0, atol=1e-15)
     assert abs(bs.phi_hat(0.0, m) - 1.0) < 1e-15
     for J in (1, 2, 3, -1):
         assert abs(bs.phi_hat(2 * np.pi * J, m)) < 1e-15
@@ -124,3 +126,10 @@ def test_phi_decay_of_bl3_coefficients():
     assert abs(c[0] - 1.9697616) < 1e-6
     assert abs(c[1] - c[-1]) < 1e-15
     assert abs(c[30]) < 1e-7 and abs(c[40]) < 1e-9
+
+
+@pytest.mark.parametrize("m", [2, 3, 4])
+def test_phi_alias_sum_brute_force_converges_to_closed_form(m):
+    w = np.linspace(-np.pi, np.pi, 17)
+    err = np.abs(bs.phi_alias_sum_brute(w, m, jmax=3000) - bs.phi_alias_sum(w, m))
+    assert np.all(err < 1e-11)
