@@ -468,24 +468,37 @@ k_deposit(const Record<T> *__restrict__ rec, const uint32_t *__restrict__ offset
 }
 
 // Tile-gather deposit for FP32 grids with 32-bit integer (fixed-point) shared-memory
-// atomics, which run about three times faster than FP32 ones. Each field of the tile
-// gets a power-of-two scale 2^s with (max node value bound) * 2^s < 2^30, the bound
-// being (particles within reach of the tile) * max|q| * (largest weight product); every
-// contribution is rounded to an integer once, so a node carries an absolute error of at
-// most (contributions / 2) * 2^-s, and the sum cannot overflow.
-// Lanes take consecutive sorted particles (their stencils land in different banks); in
-// dense tiles (more than two particles per node) each thread takes a contiguous chunk
-// instead, so that lanes do not hit the same nodes at once.
+// atomics (about three times the throughput of FP32 shared atomics on this part).
+//
+// Work split: each warp walks its own contiguous chunk of the tile's particle list 32
+// at a time, lane j taking the j-th particle of each step. Sorted neighbours lie in
+// neighbouring cells, so for one stencil offset the lanes mostly hit different nodes;
+// lanes also start their y-stencil loop at offset (lane & 3), so particles that share
+// a cell hit different rows in the same instruction. Rows of the shared accumulator
+// are padded to an odd length to spread rows across banks.
+//
+// Fixed point: field f of the tile uses the scale 2^s_f with
+//   B_f 2^s_f < 2^29,   B_f = w3 min(sum |q_f|, M^2 * (largest row count) * max |q_f|),
+// over the particles within reach (w3 = the largest product of three weights; a node
+// receives from at most M^2 rows, each contributing fewer than `largest row count`
+// particles), so no node sum can overflow, and also max |q_f| w3 2^s_f < 2^22, so that
+// every contribution is rounded to an integer by one FFMA against 1.5 * 2^23 (round to
+// nearest even, one rounding of the exact product).
 template <int M, int T0, int T1, int T2, int NT>
 __global__ void __launch_bounds__(NT)
 k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__ offsets,
-             const unsigned *__restrict__ qmax_bits, int ng, int sshift, float *__restrict__ grids, int64_t grid_elems)
+             const unsigned *__restrict__ /*qmax_bits*/, int ng, int sshift, float *__restrict__ grids, int64_t grid_elems)
 {
     using C = DepositCfg<float, M, T0, T1, T2, NT>;
+    constexpr int RW = T2 + 1;  // odd row pitch
+    constexpr int TNP = T0 * T1 * RW;
+    constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    int *acc = reinterpret_cast<int *>(smem_raw);  // [4][T0][T1][T2]
+    int *acc = reinterpret_cast<int *>(smem_raw);  // [4][T0 * T1][RW]
     __shared__ uint32_t s_beg[C::MAXR];
     __shared__ uint32_t s_pre[C::MAXR + 1];
+    __shared__ float s_red[NW][8];
+    __shared__ unsigned s_rowmax;
     __shared__ float s_scale[4];
 
     const int ntz = ng / T2, nty = ng / T1;
@@ -495,73 +508,104 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
     const int ty = tile % nty;
     const int tx = tile / nty;
     const int t0 = tx * T0, t1 = ty * T1, t2 = tz * T2;
-    for (int k = threadIdx.x; k < 4 * C::TN; k += NT) acc[k] = 0;
+    for (int k = threadIdx.x; k < 4 * TNP; k += NT) acc[k] = 0;
+    if (threadIdx.x == 0) s_rowmax = 0;
     const uint32_t total = build_ranges<C>(offsets, ng, sshift, t0, t1, t2, T2, s_beg, s_pre);
+    // largest row count: a row's two pieces are slots 2r and 2r + 1
+    for (int r = threadIdx.x; 2 * r + 1 < C::MAXR + 1; r += NT) {
+        const uint32_t c = s_pre[2 * r + 2 <= C::MAXR ? 2 * r + 2 : C::MAXR] - s_pre[2 * r];
+        if (c) atomicMax(&s_rowmax, c);
+    }
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t per_warp = ((total + NW - 1) / NW + 31u) & ~31u;
+    const uint32_t wbeg = static_cast<uint32_t>(warp) * per_warp;
+    const uint32_t wend = min(wbeg + per_warp, total);
+
+    // pass 1: per-field max |q| and sum |q| (rounded up) over the tile's particles
     {
-        // sum |q| over the particles within reach, rounded up: every node value of the
-        // tile is at most kMaxWeight3 times this
-        float qs[4] = {0.f, 0.f, 0.f, 0.f};
-        for (uint32_t p = threadIdx.x; p < total; p += NT) {
-            const int slot = find_slot<C::MAXR>(s_pre, p);
+        float qm[4] = {0.f, 0.f, 0.f, 0.f}, qs[4] = {0.f, 0.f, 0.f, 0.f};
+        int slot = wbeg + lane < wend ? find_slot<C::MAXR>(s_pre, wbeg + lane) : 0;
+        for (uint32_t p = wbeg + lane; p < wend; p += 32) {
+            while (p >= s_pre[slot + 1]) ++slot;
             const Vec4<float> q = rec[s_beg[slot] + (p - s_pre[slot])].q;
-            qs[0] = __fadd_ru(qs[0], fabsf(q.x));
-            qs[1] = __fadd_ru(qs[1], fabsf(q.y));
-            qs[2] = __fadd_ru(qs[2], fabsf(q.z));
-            qs[3] = __fadd_ru(qs[3], fabsf(q.w));
-        }
-        __shared__ float s_red[NT / 32][4];
+            const float a[4] = {fabsf(q.x), fabsf(q.y), fabsf(q.z), fabsf(q.w)};
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            for (int o = 16; o > 0; o >>= 1) qs[f] = __fadd_ru(qs[f], __shfl_xor_sync(0xffffffffu, qs[f], o));
-            if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5][f] = qs[f];
+            for (int f = 0; f < 4; ++f) qm[f] = fmaxf(qm[f], a[f]), qs[f] = __fadd_ru(qs[f], a[f]);
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                qm[f] = fmaxf(qm[f], __shfl_xor_sync(0xffffffffu, qm[f], o));
+                qs[f] = __fadd_ru(qs[f], __shfl_xor_sync(0xffffffffu, qs[f], o));
+            }
+        if (lane == 0)
+#pragma unroll
+            for (int f = 0; f < 4; ++f) s_red[warp][f] = qm[f], s_red[warp][4 + f] = qs[f];
         __syncthreads();
         if (threadIdx.x < 4) {
-            float sum = 0.f;
-            for (int w = 0; w < NT / 32; ++w) sum = __fadd_ru(sum, s_red[w][threadIdx.x]);
-            // fall back to count * max|q| if the sum overflowed or is not finite
-            const float alt = static_cast<float>(total) * __uint_as_float(qmax_bits[threadIdx.x]);
-            const float bound = kMaxWeight3<M> * 1.0001f * (sum < alt && isfinite(sum) ? sum : alt);
-            int e = 0;
-            if (bound > 0.f) frexpf(bound, &e);  // bound < 2^e
-            if (!isfinite(bound)) e = 150;
-            int sexp = 30 - e;
+            const int f = threadIdx.x;
+            float m = 0.f, sum = 0.f;
+            for (int w = 0; w < NW; ++w) m = fmaxf(m, s_red[w][f]), sum = __fadd_ru(sum, s_red[w][4 + f]);
+            const float w3 = kMaxWeight3<M> * 1.0001f;
+            const float by_rows = static_cast<float>(M * M) * static_cast<float>(s_rowmax) * m;
+            const float bound = w3 * (isfinite(sum) && sum < by_rows ? sum : by_rows);
+            const float cmax = w3 * m;  // largest single contribution
+            int eb = 0, ec = 0;
+            if (bound > 0.f) frexpf(bound, &eb);  // bound < 2^eb
+            if (cmax > 0.f) frexpf(cmax, &ec);
+            if (!isfinite(bound)) eb = 150;
+            if (!isfinite(cmax)) ec = 150;
+            int sexp = min(29 - eb, 22 - ec);
             sexp = sexp > 120 ? 120 : (sexp < -120 ? -120 : sexp);
-            s_scale[threadIdx.x] = ldexpf(1.0f, sexp);
+            s_scale[f] = ldexpf(1.0f, sexp);
         }
         __syncthreads();
     }
     const float sc0 = s_scale[0], sc1 = s_scale[1], sc2 = s_scale[2], sc3 = s_scale[3];
+    constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+    constexpr int kMagicBits = 0x4B400000;
+    const int rot = lane & 3;
 
-    const bool dense = total > 2u * C::TN;
-    const uint32_t chunk = (total + NT - 1) / NT;
-    const uint32_t pbeg = dense ? threadIdx.x * chunk : threadIdx.x;
-    const uint32_t pend = dense ? min(pbeg + chunk, total) : total;
-    const uint32_t pstep = dense ? 1u : static_cast<uint32_t>(NT);
-    for (uint32_t p = pbeg; p < pend; p += pstep) {
-        const int slot = find_slot<C::MAXR>(s_pre, p);
-        const Record<float> r = rec[s_beg[slot] + (p - s_pre[slot])];
-        float w[3][M];
-        int li[3][M];
-        stencil<float, M>(r, ng, t0, t1, t2, T0, T1, T2, w, li);
-        const float q0 = r.q.x * sc0, q1 = r.q.y * sc1, q2 = r.q.z * sc2, q3 = r.q.w * sc3;
+    // pass 2: deposit
+    {
+        int slot = wbeg + lane < wend ? find_slot<C::MAXR>(s_pre, wbeg + lane) : 0;
+        for (uint32_t p = wbeg + lane; p < wend; p += 32) {
+            while (p >= s_pre[slot + 1]) ++slot;
+            const Record<float> rc = rec[s_beg[slot] + (p - s_pre[slot])];
+            float w[3][M];
+            int li[3][M];
+            stencil<float, M>(rc, ng, t0, t1, t2, T0, T1, T2, w, li);
+            // rotate the y stencil by `rot` (lanes sharing a cell then hit different rows)
+            float wy[M];
+            int ly[M];
 #pragma unroll
-        for (int k0 = 0; k0 < M; ++k0) {
-            if (li[0][k0] < 0) continue;
+            for (int k = 0; k < M; ++k) {
+                const int kk0 = k, kk1 = (k + 1) % M, kk2 = (k + 2) % M, kk3 = (k + 3) % M;
+                const int rr = rot % M;
+                wy[k] = rr == 0 ? w[1][kk0] : rr == 1 ? w[1][kk1] : rr == 2 ? w[1][kk2] : w[1][kk3];
+                ly[k] = rr == 0 ? li[1][kk0] : rr == 1 ? li[1][kk1] : rr == 2 ? li[1][kk2] : li[1][kk3];
+            }
+            const float q0 = rc.q.x * sc0, q1 = rc.q.y * sc1, q2 = rc.q.z * sc2, q3 = rc.q.w * sc3;
 #pragma unroll
-            for (int k1 = 0; k1 < M; ++k1) {
-                if (li[1][k1] < 0) continue;
-                const float w01 = w[0][k0] * w[1][k1];
-                const int b01 = (li[0][k0] * T1 + li[1][k1]) * T2;
+            for (int k0 = 0; k0 < M; ++k0) {
+                if (li[0][k0] < 0) continue;
 #pragma unroll
-                for (int k2 = 0; k2 < M; ++k2) {
-                    if (li[2][k2] < 0) continue;
-                    const float ww = w01 * w[2][k2];
-                    int *a = acc + b01 + li[2][k2];
-                    atomicAdd(a, __float2int_rn(q0 * ww));
-                    atomicAdd(a + C::TN, __float2int_rn(q1 * ww));
-                    atomicAdd(a + 2 * C::TN, __float2int_rn(q2 * ww));
-                    atomicAdd(a + 3 * C::TN, __float2int_rn(q3 * ww));
+                for (int k1 = 0; k1 < M; ++k1) {
+                    if (ly[k1] < 0) continue;
+                    const float w01 = w[0][k0] * wy[k1];
+                    const int b01 = (li[0][k0] * T1 + ly[k1]) * RW;
+#pragma unroll
+                    for (int k2 = 0; k2 < M; ++k2) {
+                        if (li[2][k2] < 0) continue;
+                        const float ww = w01 * w[2][k2];
+                        int *a = acc + b01 + li[2][k2];
+                        atomicAdd(a, __float_as_int(fmaf(q0, ww, kMagic)) - kMagicBits);
+                        atomicAdd(a + TNP, __float_as_int(fmaf(q1, ww, kMagic)) - kMagicBits);
+                        atomicAdd(a + 2 * TNP, __float_as_int(fmaf(q2, ww, kMagic)) - kMagicBits);
+                        atomicAdd(a + 3 * TNP, __float_as_int(fmaf(q3, ww, kMagic)) - kMagicBits);
+                    }
                 }
             }
         }
@@ -572,8 +616,9 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
         const int l2 = k % T2, l01 = k / T2;
         const int l1 = l01 % T1, l0 = l01 / T1;
         const int64_t gi = (static_cast<int64_t>(t0 + l0) * ng + (t1 + l1)) * (ng + 2) + t2 + l2;
+        const int ai = l01 * RW + l2;
 #pragma unroll
-        for (int f = 0; f < 4; ++f) grids[f * grid_elems + gi] = static_cast<float>(acc[f * C::TN + k]) * inv[f];
+        for (int f = 0; f < 4; ++f) grids[f * grid_elems + gi] = static_cast<float>(acc[f * TNP + ai]) * inv[f];
     }
 }
 
@@ -597,21 +642,26 @@ cudaError_t launch_deposit_t(const AssignPlan &pl, const uint32_t *offsets, cons
 {
     using C = DepositCfg<T, M, T0, T1, T2, NT>;
     void (*kern)(const Record<T> *, const uint32_t *, const unsigned *, int, int, T *, int64_t);
-    if constexpr (sizeof(T) == 4) kern = k_deposit_fx<M, T0, T1, T2, NT>;
-    else kern = k_deposit<T, M, T0, T1, T2, NT>;
+    size_t smem = C::smem;
+    if constexpr (sizeof(T) == 4) {
+        kern = k_deposit_fx<M, T0, T1, T2, NT>;
+        smem = size_t(4) * T0 * T1 * (T2 + 1) * sizeof(int);
+    } else {
+        kern = k_deposit<T, M, T0, T1, T2, NT>;
+    }
     static int configured_device = -1;  // the attribute is per device
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (configured_device != dev) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(C::smem));
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
         configured_device = dev;
     }
     const int ng = pl.ng;
     const int64_t tiles = static_cast<int64_t>(ng / T0) * (ng / T1) * (ng / T2);
     const int64_t grid_elems = static_cast<int64_t>(ng) * ng * (ng + 2);
-    kern<<<static_cast<unsigned>(tiles), NT, C::smem, s>>>(rec, offsets, qmax, ng, pl.sshift, static_cast<T *>(grids),
+    kern<<<static_cast<unsigned>(tiles), NT, smem, s>>>(rec, offsets, qmax, ng, pl.sshift, static_cast<T *>(grids),
                                                            grid_elems);
     return cudaGetLastError();
 }
@@ -625,7 +675,7 @@ cudaError_t launch_deposit_m(const AssignPlan &pl, const uint32_t *offsets, cons
     switch (pl.tile) {
     case 0: return launch_deposit_t<float, M, 16, 16, 16, 256>(pl, offsets, q, rf, grids, s);
     case 1: return launch_deposit_t<float, M, 16, 16, 32, 512>(pl, offsets, q, rf, grids, s);
-    case 2: return launch_deposit_t<float, M, 8, 8, 32, 256>(pl, offsets, q, rf, grids, s);
+    case 2: return launch_deposit_t<float, M, 8, 8, 32, 128>(pl, offsets, q, rf, grids, s);
     case 3: return launch_deposit_t<float, M, 8, 8, 8, 128>(pl, offsets, q, rf, grids, s);
     case 4: return launch_deposit_t<double, M, 8, 8, 16, 256>(pl, offsets, q, rd, grids, s);
     case 5: return launch_deposit_t<double, M, 16, 16, 16, 256>(pl, offsets, q, rd, grids, s);
