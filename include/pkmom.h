@@ -172,6 +172,23 @@ pkmom_status pkmom_estimate(pkmom_ctx *ctx, const pkmom_catalog *cat, const pkmo
 pkmom_status pkmom_estimate_host(pkmom_ctx *ctx, const pkmom_catalog *cat_host, const pkmom_params *p,
                                  double *out_host, void *stream);
 
+/* Step 4 like pkmom_spectra, for callers that cannot allocate device memory (for
+ * example code replayed inside a CUDA graph, or a host application that owns a fixed
+ * device pool and forbids allocator calls). This one entry point has no counterpart
+ * in the paper: it exists only so that such callers can run the binning step.
+ * It allocates nothing: its scratch (shell table, window tables, partial and shell
+ * sums) is one file-scope device array of 4 MiB, held by every GPU that loads the
+ * library until the process exits. grids, moments_dev and out_dev are as for
+ * pkmom_spectra (caller-owned device memory). Limits: nbins <= 256 and the tables for
+ * ng <= 1024 must fit in 4 MiB (PKMOM_EUNSUPPORTED otherwise); other argument errors
+ * give PKMOM_EINVAL, CUDA errors PKMOM_ECUDA. The first call on a device looks up the
+ * array's device address for that device (the device must be current; make that
+ * first call before any stream capture). Every call rebuilds what it reads in the
+ * shared array, but calls whose work overlaps on the GPU race on it: order them on
+ * one stream. No context is used. */
+pkmom_status pkmom_spectra_static(const pkmom_params *p, const void *grids, const void *moments_dev,
+                                  double *out_dev, void *stream);
+
 /* Wait for the stream and return any latched device-side error (PKMOM_EDATA). */
 pkmom_status pkmom_sync(pkmom_ctx *ctx, void *stream);
 

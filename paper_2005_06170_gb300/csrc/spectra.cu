@@ -458,3 +458,198 @@ cudaError_t launch_finalize(const SpectraTables &t, const pkmom_params &p, const
 }
 
 }  // namespace pkmom
+
+// ---------------------------------------------------------------------------
+// pkmom_spectra_static: step 4 without any device allocation.
+//
+// Some callers cannot allocate device memory while they run: code inside a CUDA
+// graph that is replayed without host involvement, a host process that owns a
+// fixed memory pool and forbids allocator calls, or a plug-in that must not grow
+// the device footprint after start-up. For them this entry point keeps all of its
+// scratch (shell table, window tables, per-block partial sums, shell sums) in one
+// file-scope device array of kStaticScratchBytes. Every GPU that loads the library
+// holds that array until the process exits. The caller passes the transformed grids,
+// the moments and the output, as for pkmom_spectra.
+//
+// The first call on a device looks up the array's device address for that device
+// (cudaGetSymbolAddress) with the device current; make that first call before any
+// stream capture. All calls share the one array and each call overwrites what it
+// uses (the previous call's contents remain until then, and everything that must
+// start at zero is cleared by the call itself), so calls whose work overlaps on the
+// GPU (different streams without ordering, or several host threads) race with each
+// other.
+namespace pkmom {
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(4) << 20;  // 4 MiB
+constexpr int kStaticMaxBins = 256;
+constexpr int kStaticBlocks = 64;  // CTAs of the binning kernels on this path
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+__device__ const double kEF1[1] = {1.0};
+__device__ const double kEF2[2] = {2.0 / 3.0, 1.0 / 6.0};
+__device__ const double kEF3[3] = {11.0 / 20.0, 13.0 / 60.0, 1.0 / 120.0};
+__device__ const double kEF4[4] = {151.0 / 315.0, 397.0 / 1680.0, 1.0 / 42.0, 1.0 / 5040.0};
+
+// The shell table and the per-axis window factors, built on the device in FP64 with
+// the same expressions as build_spectra_tables (correctly rounded sqrt and division,
+// so the shell of every |n|^2 is the same).
+template <typename T>
+__global__ void k_static_tables(int ng, int order, int nbins, double umin, double umax, int nsq_max,
+                                uint16_t *__restrict__ bintab, T *__restrict__ gf, T *__restrict__ gh,
+                                double *__restrict__ hf, double *__restrict__ hh)
+{
+    const double *ef = order == 1 ? kEF1 : order == 2 ? kEF2 : order == 3 ? kEF3 : kEF4;
+    const int nh = ng / 2 + 1;
+    const int stride = gridDim.x * blockDim.x;
+    for (int nsq = blockIdx.x * blockDim.x + threadIdx.x; nsq <= nsq_max; nsq += stride) {
+        uint16_t b = 0xffff;
+        if (nsq > 0) {
+            const double u = sqrt(static_cast<double>(nsq));
+            if (u >= umin && u <= umax) {
+                double tb = floor(((u - umin) * nbins) / (umax - umin));
+                if (tb > nbins - 1) tb = nbins - 1;
+                b = static_cast<uint16_t>(tb);
+            }
+        }
+        bintab[nsq] = b;
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ng + nh; i += stride) {
+        const bool full = i < ng;
+        const int j = full ? i : i - ng;
+        const int nj = full ? (j < ng / 2 ? j : j - ng) : j;
+        const double w = kTwoPi * nj / ng;
+        double s = ef[0];
+        for (int n = 1; n < order; ++n) s += 2.0 * ef[n] * cos(n * w);
+        const double x = 0.5 * w;
+        const double sx = x == 0.0 ? 1.0 : sin(x) / x;
+        double b2 = 1.0;
+        for (int k = 0; k < order; ++k) b2 *= sx;
+        b2 *= b2;
+        if (full) {
+            gf[j] = static_cast<T>(1.0 / b2);
+            hf[j] = s / b2;
+        } else {
+            gh[j] = static_cast<T>(1.0 / b2);
+            hh[j] = s / b2;
+        }
+    }
+}
+
+size_t static_align(size_t v) { return (v + 255) / 256 * 256; }
+
+struct StaticLayout {
+    size_t bintab, gf, gh, hf, hh, partials, sums, total;
+};
+
+StaticLayout static_layout(int ng, int nbins, int nsq_max, size_t elem)
+{
+    StaticLayout L{};
+    const int nh = ng / 2 + 1;
+    size_t off = 0;
+    L.bintab = off;
+    off = static_align(off + size_t(nsq_max + 1) * sizeof(uint16_t));
+    L.gf = off;
+    off = static_align(off + size_t(ng) * elem);
+    L.gh = off;
+    off = static_align(off + size_t(nh) * elem);
+    L.hf = off;
+    off = static_align(off + size_t(ng) * sizeof(double));
+    L.hh = off;
+    off = static_align(off + size_t(nh) * sizeof(double));
+    L.partials = off;
+    off = static_align(off + size_t(kStaticBlocks) * kModeVals * nbins * sizeof(double));
+    L.sums = off;
+    off = static_align(off + size_t(kModeVals + kBinVals) * nbins * sizeof(double));
+    L.total = off;
+    return L;
+}
+
+// Device address of g_static_scratch, looked up once per device.
+constexpr int kMaxDevices = 64;
+unsigned char *g_static_ptr[kMaxDevices] = {};
+
+cudaError_t static_scratch_ptr(unsigned char **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (!g_static_ptr[dev]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_ptr[dev] = static_cast<unsigned char *>(ptr);
+    }
+    *out = g_static_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace pkmom
+
+extern "C" pkmom_status pkmom_spectra_static(const pkmom_params *p, const void *grids, const void *moments_dev,
+                                             double *out_dev, void *stream)
+{
+    using namespace pkmom;
+    if (!p || !grids || !moments_dev || !out_dev) return PKMOM_EINVAL;
+    if (!(p->box_L > 0) || p->ng < 16 || p->ng > 1024 || p->ng % 8 || p->order < 1 || p->order > 4 ||
+        (p->precision != PKMOM_F32 && p->precision != PKMOM_F64) || p->nbins < 1 || p->theta_sn_mode < 0 ||
+        p->theta_sn_mode > 1)
+        return PKMOM_EINVAL;
+    if (p->nbins > kStaticMaxBins) return PKMOM_EUNSUPPORTED;  // beyond the static scratch's shell limit
+    const double umin = p->kmin_kf > 0 ? p->kmin_kf : 1.0;
+    const double umax = p->kmax_kf > 0 ? p->kmax_kf : 0.5 * p->ng;
+    if (!(umax <= 0.5 * p->ng) || !(umin < umax)) return PKMOM_EINVAL;
+    const int ng = p->ng, nh = ng / 2 + 1, nbins = p->nbins;
+    const int nsq_max = static_cast<int>(std::floor(umax * umax)) + 1;
+    const size_t elem = p->precision == PKMOM_F32 ? sizeof(float) : sizeof(double);
+    const StaticLayout L = static_layout(ng, nbins, nsq_max, elem);
+    if (L.total > kStaticScratchBytes) return PKMOM_EUNSUPPORTED;  // does not fit the static scratch
+    unsigned char *base = nullptr;
+    if (static_scratch_ptr(&base) != cudaSuccess) return PKMOM_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    SpectraTables t;
+    t.ng = ng;
+    t.order = p->order;
+    t.nbins = nbins;
+    t.prec = p->precision;
+    t.umin = umin;
+    t.umax = umax;
+    t.nsq_max = nsq_max;
+    t.bintab = reinterpret_cast<uint16_t *>(base + L.bintab);
+    t.g_full = base + L.gf;
+    t.g_half = base + L.gh;
+    t.h_full = reinterpret_cast<double *>(base + L.hf);
+    t.h_half = reinterpret_cast<double *>(base + L.hh);
+    t.partials = reinterpret_cast<double *>(base + L.partials);
+    t.mode_sums = reinterpret_cast<double *>(base + L.sums);
+    t.bin_blocks = kStaticBlocks;
+
+    const int tb = 256, tg = (nsq_max + 1 + tb - 1) / tb < 256 ? (nsq_max + 1 + tb - 1) / tb : 256;
+    if (p->precision == PKMOM_F32)
+        k_static_tables<float><<<tg, tb, 0, s>>>(ng, p->order, nbins, umin, umax, nsq_max, t.bintab,
+                                                 static_cast<float *>(t.g_full), static_cast<float *>(t.g_half),
+                                                 t.h_full, t.h_half);
+    else
+        k_static_tables<double><<<tg, tb, 0, s>>>(ng, p->order, nbins, umin, umax, nsq_max, t.bintab,
+                                                  static_cast<double *>(t.g_full), static_cast<double *>(t.g_half),
+                                                  t.h_full, t.h_half);
+    const uint32_t nmodes = static_cast<uint32_t>(static_cast<int64_t>(ng) * ng * nh);
+    const size_t msmem = static_cast<size_t>(kModeVals) * nbins * sizeof(double);
+    if (cudaFuncSetAttribute(k_mode_sums, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(msmem)) !=
+        cudaSuccess)
+        return PKMOM_ECUDA;
+    // every partial slot is written by its block, so nothing here needs clearing
+    k_mode_sums<<<kStaticBlocks, kBinThreads, msmem, s>>>(ng, nmodes, t.bintab, t.nsq_max, t.h_full, t.h_half, nbins,
+                                                          t.partials);
+    k_reduce_partials<kModeVals><<<nbins, 256, 0, s>>>(t.partials, kStaticBlocks, nbins, t.mode_sums);
+    LaunchStats st;
+    if (cudaGetLastError() != cudaSuccess) return PKMOM_ECUDA;
+    if (launch_bin(t, grids, static_cast<const double *>(moments_dev), s, st) != cudaSuccess) return PKMOM_ECUDA;
+    if (launch_finalize(t, *p, static_cast<const double *>(moments_dev), out_dev, s, st) != cudaSuccess)
+        return PKMOM_ECUDA;
+    return PKMOM_OK;
+}

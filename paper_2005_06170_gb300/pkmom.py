@@ -78,6 +78,7 @@ def lib():
         "pkmom_timing_enable": (i32, [vp, i32]),
         "pkmom_timing_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
         "pkmom_kernel_launches": (i64, [vp]),
+        "pkmom_spectra_static": (i32, [ctypes.POINTER(Params), vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -90,7 +91,7 @@ def lib():
 EXPORTED = ("pkmom_params_default", "pkmom_create", "pkmom_destroy", "pkmom_strerror", "pkmom_last_error",
             "pkmom_grid_bytes", "pkmom_assign_scratch_bytes", "pkmom_footprint_bytes", "pkmom_assign",
             "pkmom_fft", "pkmom_spectra", "pkmom_estimate", "pkmom_estimate_host", "pkmom_sync",
-            "pkmom_timing_enable", "pkmom_timing_read", "pkmom_kernel_launches")
+            "pkmom_timing_enable", "pkmom_timing_read", "pkmom_kernel_launches", "pkmom_spectra_static")
 
 
 def params(box_L: float, ng: int, nbins: int, *, order: int = 4, precision: int = F32, kmin_kf: float = 1.0,
@@ -249,6 +250,15 @@ class Context:
 
     def kernel_launches(self) -> int:
         return int(lib().pkmom_kernel_launches(self._h))
+
+
+def spectra_static(p: Params, grids, moments, out, stream=None):
+    """pkmom_spectra_static: the binning step without any device allocation (its scratch
+    is a fixed device array inside the library); see include/pkmom.h."""
+    st = lib().pkmom_spectra_static(ctypes.byref(p), grids.data_ptr(), moments.data_ptr(), out.data_ptr(),
+                                    _stream_ptr(stream))
+    if st != 0:
+        raise PkmomError(st, lib().pkmom_strerror(st).decode())
 
 
 def as_dict(out) -> dict:
