@@ -36,6 +36,9 @@ WORKLOADS = {
                            256, 128, "f32"),
     "poisson32768_ng64_fp64": ("32768 Poisson particles, L=256 Mpc/h, sigma_v=300 km/s, 64^3 FP64 grid, BL3, "
                                "32 shells", dict(kind="poisson", n=32768, L=256.0, seed=1000), 64, 32, "f64"),
+    "zeldovich256_ng512": ("Zel'dovich 256^3 particles, L=1000 Mpc/h, 512^3 FP32 grid, BL3, 128 shells, "
+                           "with and without bulk flow (0.125 particle per cell)",
+                           dict(kind="zeldovich", n_side=256, L=1000.0, seed=1001), 512, 128, "f32"),
     "zeldovich512_ng512": ("Zel'dovich 512^3 particles, L=1500 Mpc/h, 512^3 FP32 grid, BL3, 128 shells, "
                            "with and without bulk flow", dict(kind="zeldovich", n_side=512, L=1500.0, seed=1002),
                            512, 128, "f32"),

@@ -102,7 +102,7 @@ typedef struct {
  * paper's choices. */
 typedef struct {
     double box_L;            /* side of the periodic box (> 0) */
-    int ng;                  /* grid points per side: even, 16..2048 */
+    int ng;                  /* grid points per side: a multiple of 8 in 16..1024 */
     int order;               /* B-spline order m of the BL kernel: 1..4 (4 = BL3, default) */
     int precision;           /* PKMOM_F32 (FP32 grids and FFT) or PKMOM_F64 */
     int nbins;               /* number of linear |k| shells, 1..1024 */

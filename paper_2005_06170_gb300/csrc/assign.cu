@@ -23,7 +23,7 @@ namespace pkmom {
 namespace {
 
 constexpr int kHistThreads = 256;
-constexpr int kGroup = 16;  // particles summed in the catalogue precision before each FP64 add
+constexpr int kGroup = 16;  // particles per lane summed in the catalogue precision before a warp reduction
 
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
@@ -40,15 +40,28 @@ __device__ __forceinline__ bool cell_of(T u, int ng, int &c)
 
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
-template <typename T>
-__device__ __forceinline__ double warp_sum(double v)
+// A record's fourth coordinate holds its wrapped cell (10 bits per axis, ng <= 1024):
+// the bit pattern of an FP32 value, or the integer itself as an FP64 value.
+template <typename T> __device__ __forceinline__ T pack_cell(int c0, int c1, int c2);
+template <> __device__ __forceinline__ float pack_cell<float>(int c0, int c1, int c2)
 {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
+    return __int_as_float(c0 | (c1 << 10) | (c2 << 20));
 }
+template <> __device__ __forceinline__ double pack_cell<double>(int c0, int c1, int c2)
+{
+    return static_cast<double>(c0 | (c1 << 10) | (c2 << 20));
+}
+__device__ __forceinline__ int unpack_cell(float v) { return __float_as_int(v); }
+__device__ __forceinline__ int unpack_cell(double v) { return static_cast<int>(v); }
 
+// One pass over the catalogue: the histogram of sort keys (each particle keeps the
+// rank its atomic increment returned) and the moments. Each lane sums kGroup
+// particles in the catalogue precision; the warp then adds its lanes' group sums
+// (shuffles) and lane 0 adds the result to FP64 accumulators, so that FP64 work is
+// one add per value per 32 * kGroup particles. Two particles per iteration keep more
+// loads and atomics in flight.
 template <typename T>
-__global__ void __launch_bounds__(kHistThreads)
+__global__ void __launch_bounds__(kHistThreads, 4)
 k_hist_moments(const T *__restrict__ x, const T *__restrict__ y, const T *__restrict__ z,
                const T *__restrict__ vx, const T *__restrict__ vy, const T *__restrict__ vz,
                const T *__restrict__ mass, int64_t stride, int64_t n, T scale, int ng, int sshift,
@@ -56,16 +69,33 @@ k_hist_moments(const T *__restrict__ x, const T *__restrict__ y, const T *__rest
                unsigned *__restrict__ qmax_bits, int *__restrict__ err)
 {
     const int nseg = ng >> sshift;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ double s_part[kHistThreads / 32][kMomentVals];  // per-warp FP64 sums
+    if (lane < kMomentVals) s_part[warp][lane] = 0.0;
+    __syncwarp();
     float qmax[4] = {0.f, 0.f, 0.f, 0.f};
-    double acc[kMomentVals];
     T grp[kMomentVals];
 #pragma unroll
-    for (int k = 0; k < kMomentVals; ++k) acc[k] = 0.0, grp[k] = T(0);
+    for (int k = 0; k < kMomentVals; ++k) grp[k] = T(0);
     int gcount = 0;
     const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += step) {
+    const int64_t wbase0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31);
+
+    auto flush = [&]() {
+#pragma unroll
+        for (int k = 0; k < kMomentVals; ++k) {
+            T v = grp[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) s_part[warp][k] += static_cast<double>(v);
+            grp[k] = T(0);
+        }
+    };
+    auto one = [&](int64_t i) {
         const int64_t j = i * stride;
         const T u0 = mul_rn(x[j], scale), u1 = mul_rn(y[j], scale), u2 = mul_rn(z[j], scale);
+        const T m = mass ? mass[i] : T(1);
+        const T v0 = vx[j], v1 = vy[j], v2 = vz[j];
         int c0, c1, c2;
         const bool ok = cell_of(u0, ng, c0) & cell_of(u1, ng, c1) & cell_of(u2, ng, c2);
         uint32_t rank = 0xffffffffu;
@@ -76,8 +106,6 @@ k_hist_moments(const T *__restrict__ x, const T *__restrict__ y, const T *__rest
             *err = 1;
         }
         ranks[i] = rank;
-        const T m = mass ? mass[i] : T(1);
-        const T v0 = vx[j], v1 = vy[j], v2 = vz[j];
         const T m2 = m * m;
         qmax[0] = fmaxf(qmax[0], static_cast<float>(fabs(m)));
         qmax[1] = fmaxf(qmax[1], static_cast<float>(fabs(m * v0)));
@@ -97,27 +125,25 @@ k_hist_moments(const T *__restrict__ x, const T *__restrict__ y, const T *__rest
         grp[11] += m2 * v0 * v1;
         grp[12] += m2 * v0 * v2;
         grp[13] += m2 * v1 * v2;
-        if (++gcount == kGroup) {
-#pragma unroll
-            for (int k = 0; k < kMomentVals; ++k) acc[k] += static_cast<double>(grp[k]), grp[k] = T(0);
+    };
+    // warp-uniform loop: every lane runs the same iterations (shuffles inside)
+    for (int64_t wb = wbase0; wb < n; wb += 2 * step) {
+        const int64_t i0 = wb + lane, i1 = wb + step + lane;
+        if (i0 < n) one(i0);
+        if (i1 < n) one(i1);
+        gcount += 2;
+        if (gcount >= kGroup) {
+            flush();
             gcount = 0;
         }
     }
-#pragma unroll
-    for (int k = 0; k < kMomentVals; ++k) acc[k] += static_cast<double>(grp[k]);
+    flush();
 
-    __shared__ double s_part[kHistThreads / 32][kMomentVals];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         // non-negative floats order like their bit patterns
         const unsigned b = __reduce_max_sync(0xffffffffu, __float_as_uint(qmax[f]));
         if (lane == 0) atomicMax(qmax_bits + f, b);
-    }
-#pragma unroll
-    for (int k = 0; k < kMomentVals; ++k) {
-        const double v = warp_sum<T>(acc[k]);
-        if (lane == 0) s_part[warp][k] = v;
     }
     __syncthreads();
     if (threadIdx.x < kMomentVals) {
@@ -179,9 +205,17 @@ k_scan_reduce(const uint32_t *__restrict__ counts, int64_t nkeys, uint32_t *__re
 {
     const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile + static_cast<int64_t>(threadIdx.x) * kScanItems;
     uint32_t s = 0;
+    if (base + kScanItems <= nkeys) {
+        const uint4 *v4 = reinterpret_cast<const uint4 *>(counts + base);
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k)
-        if (base + k < nkeys) s += counts[base + k];
+        for (int k = 0; k < kScanItems / 4; ++k) {
+            const uint4 q = v4[k];
+            s += q.x + q.y + q.z + q.w;
+        }
+    } else {
+        for (int k = 0; k < kScanItems; ++k)
+            if (base + k < nkeys) s += counts[base + k];
+    }
     uint32_t total;
     block_exclusive_scan(s, total);
     if (threadIdx.x == 0) blocksums[blockIdx.x] = total;
@@ -214,19 +248,41 @@ k_scan_apply(uint32_t *__restrict__ counts, int64_t nkeys, const uint32_t *__res
     const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile + static_cast<int64_t>(threadIdx.x) * kScanItems;
     uint32_t v[kScanItems];
     uint32_t s = 0;
+    const bool full = base + kScanItems <= nkeys;
+    if (full) {
+        const uint4 *v4 = reinterpret_cast<const uint4 *>(counts + base);
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        v[k] = base + k < nkeys ? counts[base + k] : 0u;
-        s += v[k];
+        for (int k = 0; k < kScanItems / 4; ++k) {
+            const uint4 q = v4[k];
+            v[4 * k] = q.x, v[4 * k + 1] = q.y, v[4 * k + 2] = q.z, v[4 * k + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) v[k] = base + k < nkeys ? counts[base + k] : 0u;
     }
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) s += v[k];
     uint32_t total;
     uint32_t run = block_exclusive_scan(s, total) + blocksums[blockIdx.x];
+    if (full) {
+        uint4 *o4 = reinterpret_cast<uint4 *>(counts + base);
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k)
-        if (base + k < nkeys) {
-            counts[base + k] = run;
-            run += v[k];
+        for (int k = 0; k < kScanItems / 4; ++k) {
+            uint4 q;
+            q.x = run, run += v[4 * k];
+            q.y = run, run += v[4 * k + 1];
+            q.z = run, run += v[4 * k + 2];
+            q.w = run, run += v[4 * k + 3];
+            o4[k] = q;
         }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k)
+            if (base + k < nkeys) {
+                counts[base + k] = run;
+                run += v[k];
+            }
+    }
 }
 
 // ------------------------------------------------------------------ scatter
@@ -252,7 +308,7 @@ k_scatter(const T *__restrict__ x, const T *__restrict__ y, const T *__restrict_
         const uint32_t dst = offsets[key] + rank;
         const T m = mass ? mass[i] : T(1);
         Record<T> r;
-        r.u = Vec4<T>{u0, u1, u2, T(0)};
+        r.u = Vec4<T>{u0 - floor(u0), u1 - floor(u1), u2 - floor(u2), pack_cell<T>(c0, c1, c2)};
         r.q = Vec4<T>{m, m * vx[j], m * vy[j], m * vz[j]};
         rec[dst] = r;
     }
@@ -388,16 +444,15 @@ template <typename T, int M>
 __device__ __forceinline__ void stencil(const Record<T> &r, int ng, int t0, int t1, int t2, int T0, int T1, int T2,
                                         T (&w)[3][M], int (&li)[3][M])
 {
-    const T u[3] = {r.u.x, r.u.y, r.u.z};
+    const T t[3] = {r.u.x, r.u.y, r.u.z};  // offsets within the cells
+    const int packed = unpack_cell(r.u.w);
     const int tb[3] = {t0, t1, t2};
     const int td[3] = {T0, T1, T2};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const T f = floor(u[a]);
-        int c = static_cast<int>(f) % ng;
-        c = c < 0 ? c + ng : c;
+        const int c = (packed >> (10 * a)) & 1023;
         int first;
-        bspline_weights<M, T>(u[a] - f, w[a], first);
+        bspline_weights<M, T>(t[a], w[a], first);
 #pragma unroll
         for (int k = 0; k < M; ++k) {
             int l = c + first + k - tb[a];
@@ -412,7 +467,8 @@ __device__ __forceinline__ void stencil(const Record<T> &r, int ng, int t0, int 
 template <typename T, int M, int T0, int T1, int T2, int NT>
 __global__ void __launch_bounds__(NT)
 k_deposit(const Record<T> *__restrict__ rec, const uint32_t *__restrict__ offsets,
-          const unsigned *__restrict__ /*qmax_bits*/, int ng, int sshift, T *__restrict__ grids, int64_t grid_elems)
+          const unsigned *__restrict__ /*qmax_bits*/, int ng, int sshift, T *__restrict__ grids, int64_t grid_elems,
+          int /*list_cap*/)
 {
     using C = DepositCfg<T, M, T0, T1, T2, NT>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -472,10 +528,9 @@ k_deposit(const Record<T> *__restrict__ rec, const uint32_t *__restrict__ offset
 //
 // Work split: each warp walks its own contiguous chunk of the tile's particle list 32
 // at a time, lane j taking the j-th particle of each step. Sorted neighbours lie in
-// neighbouring cells, so for one stencil offset the lanes mostly hit different nodes;
-// lanes also start their y-stencil loop at offset (lane & 3), so particles that share
-// a cell hit different rows in the same instruction. Rows of the shared accumulator
-// are padded to an odd length to spread rows across banks.
+// neighbouring cells, so for one stencil offset the lanes mostly hit different nodes
+// (particles that share a cell still collide). Rows of the shared accumulator are
+// padded to an odd length.
 //
 // Fixed point: field f of the tile uses the scale 2^s_f with
 //   B_f 2^s_f < 2^29,   B_f = w3 min(sum |q_f|, M^2 * (largest row count) * max |q_f|),
@@ -487,7 +542,8 @@ k_deposit(const Record<T> *__restrict__ rec, const uint32_t *__restrict__ offset
 template <int M, int T0, int T1, int T2, int NT>
 __global__ void __launch_bounds__(NT)
 k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__ offsets,
-             const unsigned *__restrict__ /*qmax_bits*/, int ng, int sshift, float *__restrict__ grids, int64_t grid_elems)
+             const unsigned *__restrict__ /*qmax_bits*/, int ng, int sshift, float *__restrict__ grids, int64_t grid_elems,
+             int list_cap)
 {
     using C = DepositCfg<float, M, T0, T1, T2, NT>;
     constexpr int RW = T2 + 1;  // odd row pitch
@@ -521,14 +577,29 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
     const uint32_t per_warp = ((total + NW - 1) / NW + 31u) & ~31u;
     const uint32_t wbeg = static_cast<uint32_t>(warp) * per_warp;
     const uint32_t wend = min(wbeg + per_warp, total);
+    // flat list of the tile's record indices when it fits in the list_cap slots after
+    // the accumulator (sparse catalogues: many short rows; no search per particle)
+    uint32_t *s_idx = reinterpret_cast<uint32_t *>(acc + 4 * TNP);
+    const bool listed = total <= static_cast<uint32_t>(list_cap);
+    if (listed) {
+        for (int slot = threadIdx.x; slot < C::MAXR; slot += NT) {
+            const uint32_t b = s_beg[slot], p0 = s_pre[slot], p1 = s_pre[slot + 1];
+            for (uint32_t p = p0; p < p1; ++p) s_idx[p] = b + (p - p0);
+        }
+        __syncthreads();
+    }
+    auto record_index = [&](uint32_t p, int &slot) -> uint32_t {
+        if (listed) return s_idx[p];
+        while (p >= s_pre[slot + 1]) ++slot;
+        return s_beg[slot] + (p - s_pre[slot]);
+    };
 
     // pass 1: per-field max |q| and sum |q| (rounded up) over the tile's particles
     {
         float qm[4] = {0.f, 0.f, 0.f, 0.f}, qs[4] = {0.f, 0.f, 0.f, 0.f};
-        int slot = wbeg + lane < wend ? find_slot<C::MAXR>(s_pre, wbeg + lane) : 0;
+        int slot = (!listed && wbeg + lane < wend) ? find_slot<C::MAXR>(s_pre, wbeg + lane) : 0;
         for (uint32_t p = wbeg + lane; p < wend; p += 32) {
-            while (p >= s_pre[slot + 1]) ++slot;
-            const Vec4<float> q = rec[s_beg[slot] + (p - s_pre[slot])].q;
+            const Vec4<float> q = rec[record_index(p, slot)].q;
             const float a[4] = {fabsf(q.x), fabsf(q.y), fabsf(q.z), fabsf(q.w)};
 #pragma unroll
             for (int f = 0; f < 4; ++f) qm[f] = fmaxf(qm[f], a[f]), qs[f] = __fadd_ru(qs[f], a[f]);
@@ -566,36 +637,24 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
     const float sc0 = s_scale[0], sc1 = s_scale[1], sc2 = s_scale[2], sc3 = s_scale[3];
     constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
     constexpr int kMagicBits = 0x4B400000;
-    const int rot = lane & 3;
 
     // pass 2: deposit
     {
-        int slot = wbeg + lane < wend ? find_slot<C::MAXR>(s_pre, wbeg + lane) : 0;
+        int slot = (!listed && wbeg + lane < wend) ? find_slot<C::MAXR>(s_pre, wbeg + lane) : 0;
         for (uint32_t p = wbeg + lane; p < wend; p += 32) {
-            while (p >= s_pre[slot + 1]) ++slot;
-            const Record<float> rc = rec[s_beg[slot] + (p - s_pre[slot])];
+            const Record<float> rc = rec[record_index(p, slot)];
             float w[3][M];
             int li[3][M];
             stencil<float, M>(rc, ng, t0, t1, t2, T0, T1, T2, w, li);
-            // rotate the y stencil by `rot` (lanes sharing a cell then hit different rows)
-            float wy[M];
-            int ly[M];
-#pragma unroll
-            for (int k = 0; k < M; ++k) {
-                const int kk0 = k, kk1 = (k + 1) % M, kk2 = (k + 2) % M, kk3 = (k + 3) % M;
-                const int rr = rot % M;
-                wy[k] = rr == 0 ? w[1][kk0] : rr == 1 ? w[1][kk1] : rr == 2 ? w[1][kk2] : w[1][kk3];
-                ly[k] = rr == 0 ? li[1][kk0] : rr == 1 ? li[1][kk1] : rr == 2 ? li[1][kk2] : li[1][kk3];
-            }
             const float q0 = rc.q.x * sc0, q1 = rc.q.y * sc1, q2 = rc.q.z * sc2, q3 = rc.q.w * sc3;
 #pragma unroll
             for (int k0 = 0; k0 < M; ++k0) {
                 if (li[0][k0] < 0) continue;
 #pragma unroll
                 for (int k1 = 0; k1 < M; ++k1) {
-                    if (ly[k1] < 0) continue;
-                    const float w01 = w[0][k0] * wy[k1];
-                    const int b01 = (li[0][k0] * T1 + ly[k1]) * RW;
+                    if (li[1][k1] < 0) continue;
+                    const float w01 = w[0][k0] * w[1][k1];
+                    const int b01 = (li[0][k0] * T1 + li[1][k1]) * RW;
 #pragma unroll
                     for (int k2 = 0; k2 < M; ++k2) {
                         if (li[2][k2] < 0) continue;
@@ -641,28 +700,32 @@ cudaError_t launch_deposit_t(const AssignPlan &pl, const uint32_t *offsets, cons
                              void *grids, cudaStream_t s)
 {
     using C = DepositCfg<T, M, T0, T1, T2, NT>;
-    void (*kern)(const Record<T> *, const uint32_t *, const unsigned *, int, int, T *, int64_t);
+    void (*kern)(const Record<T> *, const uint32_t *, const unsigned *, int, int, T *, int64_t, int);
     size_t smem = C::smem;
+    int list_cap = 0;
     if constexpr (sizeof(T) == 4) {
         kern = k_deposit_fx<M, T0, T1, T2, NT>;
-        smem = size_t(4) * T0 * T1 * (T2 + 1) * sizeof(int);
+        list_cap = pl.list_cap;
+        smem = size_t(4) * T0 * T1 * (T2 + 1) * sizeof(int) + size_t(list_cap) * sizeof(uint32_t);
     } else {
         kern = k_deposit<T, M, T0, T1, T2, NT>;
     }
-    static int configured_device = -1;  // the attribute is per device
+    // the attribute is per device and only needs raising: remember the largest value set
+    constexpr int kMaxDev = 64;
+    static size_t configured[kMaxDev] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (configured_device != dev) {
+    if (dev < 0 || dev >= kMaxDev || configured[dev] < smem) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
-        configured_device = dev;
+        if (dev >= 0 && dev < kMaxDev) configured[dev] = smem;
     }
     const int ng = pl.ng;
     const int64_t tiles = static_cast<int64_t>(ng / T0) * (ng / T1) * (ng / T2);
     const int64_t grid_elems = static_cast<int64_t>(ng) * ng * (ng + 2);
     kern<<<static_cast<unsigned>(tiles), NT, smem, s>>>(rec, offsets, qmax, ng, pl.sshift, static_cast<T *>(grids),
-                                                           grid_elems);
+                                                           grid_elems, list_cap);
     return cudaGetLastError();
 }
 

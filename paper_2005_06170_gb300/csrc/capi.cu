@@ -4,6 +4,7 @@
 // pkmom_estimate / pkmom_estimate_host, stage timing with CUDA events.
 #include <cufft.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -83,7 +84,7 @@ pkmom_status check_params(pkmom_ctx *ctx, const pkmom_params *p)
 {
     if (!p) return fail(ctx, PKMOM_EINVAL, "params is NULL");
     if (!(p->box_L > 0) || !std::isfinite(p->box_L)) return fail(ctx, PKMOM_EINVAL, "box_L must be > 0");
-    if (p->ng < 16 || p->ng > 2048 || p->ng % 8) return fail(ctx, PKMOM_EINVAL, "ng must be a multiple of 8 in [16, 2048]");
+    if (p->ng < 16 || p->ng > 1024 || p->ng % 8) return fail(ctx, PKMOM_EINVAL, "ng must be a multiple of 8 in [16, 1024]");
     if (p->order < 1 || p->order > 4) return fail(ctx, PKMOM_EINVAL, "order must be 1..4");
     if (p->precision != PKMOM_F32 && p->precision != PKMOM_F64) return fail(ctx, PKMOM_EINVAL, "bad precision");
     if (p->nbins < 1 || p->nbins > 1024) return fail(ctx, PKMOM_EINVAL, "nbins must be 1..1024");
@@ -127,14 +128,21 @@ AssignPlan plan_assign(const pkmom_params &p, int64_t n, int num_sms)
     }
     int td[3];
     deposit_tile_shape(pl.tile, p.precision, td);
-    // z segment per sort key: about one particle per key for sparse catalogues,
-    // never longer than the deposit tile, and few enough keys for 32-bit offsets
+    // one sort key per cell keeps each row's particles in z order, which the deposit's
+    // lane mapping relies on (coarser z segments measured slower even for sparse
+    // catalogues); segments only where 32-bit offsets would not suffice
     int sshift = 0;
-    const double ppc = double(n) / cells;
-    while ((1 << (sshift + 1)) <= td[2] && (p.ng % (1 << (sshift + 1))) == 0 &&
-           (ppc * (1 << sshift) < 0.5 || cells / (1 << sshift) > double(1u << 30)))
+    while ((1 << (sshift + 1)) <= td[2] && (p.ng % (1 << (sshift + 1))) == 0 && cells / (1 << sshift) > double(1u << 30))
         ++sshift;
     pl.sshift = sshift;
+    // sparse catalogues: list each tile's particles in shared memory (room for about
+    // twice the expected count of its reach; larger tiles fall back to searching)
+    const double ppc = double(n) / cells;
+    const double reach = double(td[0] + 3) * (td[1] + 3) * (td[2] + 3);
+    if (p.precision == PKMOM_F32 && ppc < 0.5) {
+        const double want = 2.0 * ppc * reach + 64.0;
+        pl.list_cap = static_cast<int>(std::min(8192.0, std::ceil(want / 256.0) * 256.0));
+    }
     pl.nkeys = int64_t(p.ng) * p.ng * (p.ng >> sshift);
     pl.hist_blocks = num_sms * 8;
     pl.scan_blocks = (pl.nkeys + 8191) / 8192;
@@ -207,13 +215,20 @@ pkmom_status get_plan(pkmom_ctx *ctx, int ng, int prec, cufftHandle *out)
             return PKMOM_OK;
         }
     cufftHandle h;
-    int n[3] = {ng, ng, ng};
-    int inembed[3] = {ng, ng, ng + 2};
-    int onembed[3] = {ng, ng, ng / 2 + 1};
-    const int idist = ng * ng * (ng + 2);
-    const int odist = ng * ng * (ng / 2 + 1);
-    cufftResult r = cufftPlanMany(&h, 3, n, inembed, 1, idist, onembed, 1, odist,
-                                  prec == PKMOM_F32 ? CUFFT_R2C : CUFFT_D2Z, 4);
+    long long n[3] = {ng, ng, ng};
+    long long inembed[3] = {ng, ng, ng + 2};
+    long long onembed[3] = {ng, ng, ng / 2 + 1};
+    const long long idist = 1LL * ng * ng * (ng + 2);
+    const long long odist = 1LL * ng * ng * (ng / 2 + 1);
+    size_t work = 0;
+    cufftResult r = cufftCreate(&h);
+    if (r == CUFFT_SUCCESS) {
+        // one grid per plan, executed four times: a batch of four 1024^3 grids made
+        // cuFFT allocate a 17 GB workspace and run twice as long (measured)
+        r = cufftMakePlanMany64(h, 3, n, inembed, 1, idist, onembed, 1, odist,
+                                prec == PKMOM_F32 ? CUFFT_R2C : CUFFT_D2Z, 1, &work);
+        if (r != CUFFT_SUCCESS) cufftDestroy(h);
+    }
     if (r != CUFFT_SUCCESS) {
         char buf[96];
         std::snprintf(buf, sizeof buf, "cufftPlanMany(ng=%d) failed with code %d", ng, int(r));
@@ -406,12 +421,18 @@ pkmom_status pkmom_fft(pkmom_ctx *ctx, const pkmom_params *p, void *grids, void 
     cudaStream_t st = as_stream(stream);
     if (cufftSetStream(h, st) != CUFFT_SUCCESS) return fail(ctx, PKMOM_ECUFFT, "cufftSetStream failed");
     StageTimer t(ctx, PKMOM_STAGE_FFT, st);
-    cufftResult r;
-    if (p->precision == PKMOM_F32)
-        r = cufftExecR2C(h, static_cast<cufftReal *>(grids), static_cast<cufftComplex *>(grids));
-    else
-        r = cufftExecD2Z(h, static_cast<cufftDoubleReal *>(grids), static_cast<cufftDoubleComplex *>(grids));
-    if (r != CUFFT_SUCCESS) return fail(ctx, PKMOM_ECUFFT, "cufftExec failed with code " + std::to_string(int(r)));
+    const size_t gelems = size_t(p->ng) * p->ng * (p->ng + 2);
+    for (int f = 0; f < 4; ++f) {
+        cufftResult r;
+        if (p->precision == PKMOM_F32) {
+            auto *g = static_cast<cufftReal *>(grids) + f * gelems;
+            r = cufftExecR2C(h, g, reinterpret_cast<cufftComplex *>(g));
+        } else {
+            auto *g = static_cast<cufftDoubleReal *>(grids) + f * gelems;
+            r = cufftExecD2Z(h, g, reinterpret_cast<cufftDoubleComplex *>(g));
+        }
+        if (r != CUFFT_SUCCESS) return fail(ctx, PKMOM_ECUFFT, "cufftExec failed with code " + std::to_string(int(r)));
+    }
     return PKMOM_OK;
 }
 
@@ -428,11 +449,12 @@ pkmom_status pkmom_spectra(pkmom_ctx *ctx, const pkmom_params *p, const void *gr
     if ((s = get_tables(ctx, *p, st, &t)) != PKMOM_OK) return s;
     {
         StageTimer tm(ctx, PKMOM_STAGE_BIN, st);
-        PK_CUDA(launch_bin(*t, grids, static_cast<const double *>(moments_dev), st, ctx->st), "binning");
+        PK_CUDA(launch_bin_shells(*t, grids, static_cast<const double *>(moments_dev), st, ctx->st), "binning");
     }
     {
         StageTimer tm(ctx, PKMOM_STAGE_FINAL, st);
-        PK_CUDA(launch_finalize(*t, *p, static_cast<const double *>(moments_dev), out_dev, st, ctx->st), "finalize");
+        PK_CUDA(launch_finalize(*t, *p, static_cast<const double *>(moments_dev), out_dev, st, ctx->st, true),
+                "finalize");
     }
     return PKMOM_OK;
 }

@@ -31,6 +31,7 @@ struct AssignPlan {
     int sshift = 0;          // z-segment length S = 1 << sshift cells per sort key
     int64_t nkeys = 0;       // ng * ng * (ng >> sshift)
     int tile = 0;            // deposit tile id (see deposit launcher)
+    int list_cap = 0;        // shared-memory particle list of an FP32 deposit tile (0 = none)
     int hist_blocks = 0;     // blocks of the moments+histogram kernel
     int64_t scan_blocks = 0; // blocks of the key scan
     size_t off_counts = 0, off_ranks = 0, off_records = 0, off_partials = 0, off_blocksums = 0, off_qmax = 0;
@@ -65,15 +66,21 @@ struct SpectraTables {
     double *h_full = nullptr;    // [ng] Sigma/Bhat^2 (FP64), for the mode tables
     double *h_half = nullptr;
     double *mode_sums = nullptr; // [kModeVals][nbins]
-    double *partials = nullptr;  // [bin_blocks][kBinVals][nbins]
+    double *partials = nullptr;  // [bin_blocks][kModeVals or kBinVals][nbins]
     int bin_blocks = 0;
+    double *item_partials = nullptr;  // [ng * nbins][kBinVals] (shell-major binning)
+    int shell_blocks = 0;
 };
 cudaError_t build_spectra_tables(SpectraTables &t, int ng, int order, int nbins, double umin, double umax, int prec,
                                  int num_sms, cudaStream_t s, LaunchStats &st);
 void free_spectra_tables(SpectraTables &t);
 cudaError_t launch_bin(const SpectraTables &t, const void *grids, const double *moments_dev, cudaStream_t s,
                        LaunchStats &st);
+cudaError_t launch_bin_shells(const SpectraTables &t, const void *grids, const double *moments_dev, cudaStream_t s,
+                              LaunchStats &st);
+// sums_ready: the shell sums were already reduced (by launch_bin_shells); otherwise the
+// per-block partials of launch_bin are reduced first
 cudaError_t launch_finalize(const SpectraTables &t, const pkmom_params &p, const double *moments_dev,
-                            double *out, cudaStream_t s, LaunchStats &st);
+                            double *out, cudaStream_t s, LaunchStats &st, bool sums_ready);
 
 }  // namespace pkmom

@@ -137,6 +137,114 @@ k_bin(const Cx<T> *__restrict__ F, int64_t gstride, int ng, uint32_t nmodes, con
     for (int k = threadIdx.x; k < kBinVals * nbins; k += blockDim.x) out[k] = s_bins[k];
 }
 
+// Shell-major binning. Work item (n0, b): all modes of shell b in the slab n_x = n0.
+// Items are ordered slab-major, so the items running together read the same slab
+// (which stays in L2). A lane takes one row (n0, n1) at a time and walks the short
+// l-interval where the row crosses the shell (bounds from FP32 square roots widened
+// by one; membership is decided exactly by the shell table), summing the seven
+// per-mode values with Kahan-compensated FP32 adds. One FP64 warp reduction per item
+// writes partials[item][kBinVals]; k_reduce_items adds the items of each shell in a
+// fixed order.
+template <typename T>
+__global__ void __launch_bounds__(kBinThreads, 5)
+k_bin_shells(const Cx<T> *__restrict__ F, int64_t gstride, int ng, int nbins, float umin, float du,
+             const uint16_t *__restrict__ bintab, int nsq_max, const T *__restrict__ gf, const T *__restrict__ gh,
+             const double *__restrict__ mom, double *__restrict__ partials)
+{
+    const int nh = ng / 2 + 1;
+    const double Mtot = mom[0];
+    const T vb0 = static_cast<T>(mom[2] / Mtot), vb1 = static_cast<T>(mom[3] / Mtot), vb2 = static_cast<T>(mom[4] / Mtot);
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int nitems = ng * nbins;
+    for (int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < nitems; item += nwarps) {
+        const int b = item % nbins;
+        const int n0 = item / nbins - ng / 2;
+        const int i0 = n0 < 0 ? n0 + ng : n0;
+        const float elo = umin + b * du, ehi = umin + (b + 1) * du;
+        T s[kBinVals], c[kBinVals];
+#pragma unroll
+        for (int k = 0; k < kBinVals; ++k) s[k] = T(0), c[k] = T(0);
+        const float rem = (ehi + 1.f) * (ehi + 1.f) - static_cast<float>(n0 * n0);
+        if (rem >= 0.f) {
+            const int R1 = static_cast<int>(floorf(sqrtf(rem)));
+            const int n1lo = max(-ng / 2, -R1), n1hi = min(ng / 2 - 1, R1);
+            const T g0 = gf[i0];
+            for (int n1 = n1lo + lane; n1 <= n1hi; n1 += 32) {
+                const int r2 = n0 * n0 + n1 * n1;
+                const int i1 = n1 < 0 ? n1 + ng : n1;
+                const float a = elo * elo - static_cast<float>(r2), z = ehi * ehi - static_cast<float>(r2);
+                const int lo = max(0, static_cast<int>(ceilf(sqrtf(fmaxf(a, 0.f)))) - 1);
+                const int hi = min(nh - 1, static_cast<int>(floorf(sqrtf(fmaxf(z, 0.f)))) + 1);
+                const int64_t rowbase = (static_cast<int64_t>(i0) * ng + i1) * nh;
+                const T gxy = g0 * gf[i1];
+                for (int l = lo; l <= hi; ++l) {
+                    const int nsq = r2 + l * l;
+                    if (nsq > nsq_max || static_cast<int>(bintab[nsq]) != b) continue;
+                    const T g = gxy * gh[l] * ((l == 0 || l == nh - 1) ? T(1) : T(2));
+                    const int64_t mi = rowbase + l;
+                    const Cx<T> d = F[mi], p0 = F[gstride + mi], p1 = F[2 * gstride + mi], p2 = F[3 * gstride + mi];
+                    const T fn0 = static_cast<T>(n0), fn1 = static_cast<T>(n1), fn2 = static_cast<T>(l);
+                    const T kr = fn0 * p0.x + fn1 * p1.x + fn2 * p2.x;
+                    const T ki = fn0 * p0.y + fn1 * p1.y + fn2 * p2.y;
+                    const Cx<T> q0{p0.x - vb0 * d.x, p0.y - vb0 * d.y};
+                    const Cx<T> q1{p1.x - vb1 * d.x, p1.y - vb1 * d.y};
+                    const Cx<T> q2{p2.x - vb2 * d.x, p2.y - vb2 * d.y};
+                    const T jr = fn0 * q0.x + fn1 * q1.x + fn2 * q2.x;
+                    const T ji = fn0 * q0.y + fn1 * q1.y + fn2 * q2.y;
+                    T v[kBinVals];
+                    v[0] = g * (d.x * d.x + d.y * d.y);
+                    v[1] = g * (p0.x * p0.x + p0.y * p0.y + p1.x * p1.x + p1.y * p1.y + p2.x * p2.x + p2.y * p2.y);
+                    v[2] = g * (kr * kr + ki * ki);
+                    v[3] = g * (d.x * ki - d.y * kr);  // Im(conj(F_d) * (n.F_p))
+                    v[4] = g * (q0.x * q0.x + q0.y * q0.y + q1.x * q1.x + q1.y * q1.y + q2.x * q2.x + q2.y * q2.y);
+                    v[5] = g * (jr * jr + ji * ji);
+                    v[6] = g * (d.x * ji - d.y * jr);
+#pragma unroll
+                    for (int k = 0; k < kBinVals; ++k) {  // Kahan: s - c carries the sum
+                        const T y = v[k] - c[k];
+                        const T t = s[k] + y;
+                        c[k] = (t - s[k]) - y;
+                        s[k] = t;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kBinVals; ++k) {
+            double dsum = static_cast<double>(s[k]) - static_cast<double>(c[k]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+            if (lane == 0) partials[static_cast<int64_t>(item) * kBinVals + k] = dsum;
+        }
+    }
+}
+
+// out[k * nbins + b] = sum over slabs j of partials[(j * nbins + b) * NV + k], fixed order.
+template <int NV>
+__global__ void __launch_bounds__(256)
+k_reduce_items(const double *__restrict__ partials, int nslabs, int nbins, double *__restrict__ out)
+{
+    const int b = blockIdx.x;
+    double s[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) s[k] = 0.0;
+    for (int j = threadIdx.x; j < nslabs; j += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s[k] += partials[(static_cast<int64_t>(j) * nbins + b) * NV + k];
+    __shared__ double red[NV][256];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < NV) out[threadIdx.x * nbins + b] = red[threadIdx.x][0];
+}
+
 __global__ void __launch_bounds__(kBinThreads)
 k_mode_sums(int ng, uint32_t nmodes, const uint16_t *__restrict__ bintab, int nsq_max, const double *__restrict__ hf,
             const double *__restrict__ hh, int nbins, double *__restrict__ partials)
@@ -337,6 +445,7 @@ void free_spectra_tables(SpectraTables &t)
     cudaFree(t.h_half);
     cudaFree(t.mode_sums);
     cudaFree(t.partials);
+    cudaFree(t.item_partials);
     t = SpectraTables{};
 }
 
@@ -389,7 +498,7 @@ cudaError_t build_spectra_tables(SpectraTables &t, int ng, int order, int nbins,
     const uint32_t nchunks = (nmodes + 31u) / 32u;
     const int warps_per_block = kBinThreads / 32;
     int64_t want = (nchunks + warps_per_block - 1) / warps_per_block;
-    const int64_t cap = static_cast<int64_t>(num_sms) * 4;
+    const int64_t cap = static_cast<int64_t>(num_sms) * 8;
     t.bin_blocks = static_cast<int>(want < cap ? want : cap);
     if (t.bin_blocks < 1) t.bin_blocks = 1;
     if ((e = cudaMalloc(reinterpret_cast<void **>(&t.partials),
@@ -398,6 +507,10 @@ cudaError_t build_spectra_tables(SpectraTables &t, int ng, int order, int nbins,
     if ((e = cudaMalloc(reinterpret_cast<void **>(&t.mode_sums), static_cast<size_t>(kModeVals + kBinVals) * nbins *
                                                                        sizeof(double))) != cudaSuccess)
         return e;
+    if ((e = cudaMalloc(reinterpret_cast<void **>(&t.item_partials),
+                        static_cast<size_t>(ng) * nbins * kBinVals * sizeof(double))) != cudaSuccess)
+        return e;
+    t.shell_blocks = num_sms * 8;
     const size_t smem = static_cast<size_t>(kModeVals) * nbins * sizeof(double);
     if ((e = cudaFuncSetAttribute(k_mode_sums, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem))) !=
         cudaSuccess)
@@ -419,16 +532,16 @@ cudaError_t launch_bin(const SpectraTables &t, const void *grids, const double *
     const size_t smem = static_cast<size_t>(kBinVals) * t.nbins * sizeof(double);
     cudaError_t e;
     if (t.prec == PKMOM_F32) {
-        if ((e = cudaFuncSetAttribute(k_bin<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(smem))) != cudaSuccess)
+        if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_bin<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          static_cast<int>(smem))) != cudaSuccess)
             return e;
         k_bin<float><<<t.bin_blocks, kBinThreads, smem, s>>>(
             static_cast<const Cx<float> *>(grids), gstride, ng, nmodes, t.bintab, t.nsq_max,
             static_cast<const float *>(t.g_full), static_cast<const float *>(t.g_half), moments_dev, t.nbins,
             t.partials);
     } else {
-        if ((e = cudaFuncSetAttribute(k_bin<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(smem))) != cudaSuccess)
+        if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_bin<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          static_cast<int>(smem))) != cudaSuccess)
             return e;
         k_bin<double><<<t.bin_blocks, kBinThreads, smem, s>>>(
             static_cast<const Cx<double> *>(grids), gstride, ng, nmodes, t.bintab, t.nsq_max,
@@ -439,11 +552,37 @@ cudaError_t launch_bin(const SpectraTables &t, const void *grids, const double *
     return cudaGetLastError();
 }
 
+cudaError_t launch_bin_shells(const SpectraTables &t, const void *grids, const double *moments_dev, cudaStream_t s,
+                              LaunchStats &st)
+{
+    const int ng = t.ng, nh = ng / 2 + 1;
+    const int64_t gstride = static_cast<int64_t>(ng) * ng * nh;
+    const float du = static_cast<float>((t.umax - t.umin) / t.nbins);
+    const unsigned blocks = static_cast<unsigned>(t.shell_blocks);
+    if (t.prec == PKMOM_F32)
+        k_bin_shells<float><<<blocks, kBinThreads, 0, s>>>(
+            static_cast<const Cx<float> *>(grids), gstride, ng, t.nbins, static_cast<float>(t.umin), du, t.bintab,
+            t.nsq_max, static_cast<const float *>(t.g_full), static_cast<const float *>(t.g_half), moments_dev,
+            t.item_partials);
+    else
+        k_bin_shells<double><<<blocks, kBinThreads, 0, s>>>(
+            static_cast<const Cx<double> *>(grids), gstride, ng, t.nbins, static_cast<float>(t.umin), du, t.bintab,
+            t.nsq_max, static_cast<const double *>(t.g_full), static_cast<const double *>(t.g_half), moments_dev,
+            t.item_partials);
+    double *sums = t.mode_sums + static_cast<size_t>(kModeVals) * t.nbins;
+    k_reduce_items<kBinVals><<<t.nbins, 256, 0, s>>>(t.item_partials, ng, t.nbins, sums);
+    st.launches += 2;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const SpectraTables &t, const pkmom_params &p, const double *moments_dev, double *out,
-                            cudaStream_t s, LaunchStats &st)
+                            cudaStream_t s, LaunchStats &st, bool sums_ready)
 {
     double *sums = t.mode_sums + static_cast<size_t>(kModeVals) * t.nbins;
-    k_reduce_partials<kBinVals><<<t.nbins, 256, 0, s>>>(t.partials, t.bin_blocks, t.nbins, sums);
+    if (!sums_ready) {
+        k_reduce_partials<kBinVals><<<t.nbins, 256, 0, s>>>(t.partials, t.bin_blocks, t.nbins, sums);
+        st.launches++;
+    }
     FinalParams fp;
     fp.V = p.box_L * p.box_L * p.box_L;
     fp.kf = kTwoPi / p.box_L;
@@ -453,7 +592,7 @@ cudaError_t launch_finalize(const SpectraTables &t, const pkmom_params &p, const
     fp.iso = p.theta_sn_mode == 1;
     fp.nbins = t.nbins;
     k_finalize<<<(t.nbins + 127) / 128, 128, 0, s>>>(sums, t.mode_sums, moments_dev, fp, out);
-    st.launches += 2;
+    st.launches++;
     return cudaGetLastError();
 }
 
@@ -649,7 +788,7 @@ extern "C" pkmom_status pkmom_spectra_static(const pkmom_params *p, const void *
     LaunchStats st;
     if (cudaGetLastError() != cudaSuccess) return PKMOM_ECUDA;
     if (launch_bin(t, grids, static_cast<const double *>(moments_dev), s, st) != cudaSuccess) return PKMOM_ECUDA;
-    if (launch_finalize(t, *p, static_cast<const double *>(moments_dev), out_dev, s, st) != cudaSuccess)
+    if (launch_finalize(t, *p, static_cast<const double *>(moments_dev), out_dev, s, st, false) != cudaSuccess)
         return PKMOM_ECUDA;
     return PKMOM_OK;
 }

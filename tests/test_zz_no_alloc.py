@@ -52,8 +52,10 @@ def test_static_scratch_spectra_match_regular_spectra_twice(gpu_lib, prec):
         pk.spectra_static(p, grids, mom, out)
         torch.cuda.synchronize()
         got = out.cpu().numpy()
-        # the same per-mode values summed in another order: FP64 rounding only
-        np.testing.assert_allclose(got, ref, rtol=1e-9, atol=1e-9 * np.nanmax(np.abs(ref)), equal_nan=True)
+        # the same per-mode values, summed in another order (and, with FP32 grids, by
+        # another reduction kernel): the suite's parity tolerance for each precision
+        rtol = 1e-4 if prec == "f32" else 1e-9
+        np.testing.assert_allclose(got, ref, rtol=rtol, atol=rtol * np.nanmax(np.abs(ref)), equal_nan=True)
     ctx.close()
 
 
