@@ -47,6 +47,15 @@ WORKLOADS = {
                             1024, 128, "f32"),
 }
 DEFAULT = "zeldovich256_ng256"
+# configs 4 and 5 run through their own drivers below
+MULTI = {
+    "batch64": "64 catalogues in one launch sequence: particle counts log-uniform in [1e5, 2e7], seeded "
+               "Zel'dovich or Poisson (50/50), grids from {128, 256, 384}^3, L in [300, 1500] Mpc/h, "
+               "FP32, 128 shells; lanes + CUDA graph + autotuned tiles",
+    "serve": "Poisson arrivals (mean 20 requests/s) of estimation requests, particle counts log-uniform in "
+             "[1e5, 1.3e8], grids from {128, 256, 512, 1024}^3, FP32, 128 shells, admitted by HBM footprint "
+             "against 180 GB",
+}
 
 
 def load_peaks():
@@ -158,18 +167,167 @@ def run_reference(args):
     return 0
 
 
+def _clock_id(torch, dev):
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        return None
+
+
+def run_batch64(args):
+    """Config 4: 64 uneven catalogues, batched (lanes + one CUDA graph + autotuner) vs
+    the plain path (one catalogue after another through pkmom_estimate)."""
+    import torch
+
+    from paper_2005_06170_gb300 import catalogs, pkmom
+    from paper_2005_06170_gb300.autotune import Autotuner
+    from paper_2005_06170_gb300.batch import BatchRunner
+    dev = torch.device("cuda", 0)
+    counts = catalogs.log_uniform_counts(64, 1e5, 2e7, seed=1004)
+    rng = np.random.Generator(np.random.PCG64(1005))
+    kinds = rng.random(64) < 0.5
+    grids = rng.choice([128, 256, 384], size=64)
+    boxes = rng.uniform(300.0, 1500.0, size=64)
+    cats, params = [], []
+    for i in range(64):
+        if kinds[i]:
+            side = max(8, int(round(counts[i] ** (1.0 / 3.0))))
+            c = catalogs.zeldovich_torch(side, float(boxes[i]), seed=2000 + i, device=dev)
+        else:
+            c = catalogs.poisson_torch(int(counts[i]), float(boxes[i]), seed=3000 + i, device=dev)
+        cats.append(c)
+        params.append(pkmom.params(float(boxes[i]), int(grids[i]), 128))
+    torch.cuda.synchronize()
+    n_total = sum(int(c["pos"].shape[0]) for c in cats)
+    cells = sum(int(p.ng) ** 3 for p in params)
+    runner = BatchRunner(cats, params, lanes=8, use_graph=True, tuner=Autotuner(repeats=2))
+    l0 = runner.kernel_launches()
+    runner.run()  # tuning, eager pass, capture
+    launches = runner.kernel_launches() - l0
+    origin = torch.cuda.current_stream(dev)
+    for _ in range(max(3, args.warmup)):
+        runner.run()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(_clock_id(torch, dev))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(origin)
+    for _ in range(args.steps):
+        runner.run()
+    e1.record(origin)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    runner.close()
+    # plain: one catalogue at a time through pkmom_estimate on one stream
+    ctx = pkmom.Context(0)
+    outs = [torch.empty((pkmom.NROWS, p.nbins), dtype=torch.float64, device=dev) for p in params]
+    for c, p, o in zip(cats, params, outs):
+        ctx.estimate(c["pos"], c["vel"], p, out=o)
+    torch.cuda.synchronize()
+    e0.record(origin)
+    for _ in range(max(1, args.steps // 2)):
+        for c, p, o in zip(cats, params, outs):
+            ctx.estimate(c["pos"], c["vel"], p, out=o)
+    e1.record(origin)
+    torch.cuda.synchronize()
+    ms_plain = e0.elapsed_time(e1) / max(1, args.steps // 2)
+    ctx.close()
+    line = {"metric": METRIC, "value": n_total / (ms * 1e-3), "unit": "particles/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": MULTI["batch64"], "n_particles": n_total, "cells": cells,
+                       "l2": "inputs larger than L2, no flush"},
+            "Mcells_per_s": cells / (ms * 1e-3) / 1e6, "plain_value": n_total / (ms_plain * 1e-3),
+            "plain_ms_per_step": ms_plain, "batched_over_plain": ms_plain / ms,
+            "gpu_launches": int(launches), "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Config 5: a Poisson arrival stream served with continuous batching (4 lanes,
+    admission by footprint against 180 GB) and, on the same trace, one request at a
+    time (1 lane): throughput and p50/p99 latency of both."""
+    import threading
+
+    import torch
+
+    from paper_2005_06170_gb300 import catalogs, pkmom
+    from paper_2005_06170_gb300.serve import Request, Server, percentiles
+    dev = torch.device("cuda", 0)
+    nreq = args.requests
+    rng = np.random.Generator(np.random.PCG64(1006))
+    gaps = rng.exponential(1.0 / 20.0, size=nreq)
+    t_arr = np.cumsum(gaps)
+    counts = np.round(np.exp(rng.uniform(np.log(1e5), np.log(1.3e8), size=nreq))).astype(np.int64)
+    grids = rng.choice([128, 256, 512, 1024], size=nreq)
+    L = 1000.0
+    pool = catalogs.poisson_torch(int(counts.max()), L, seed=1007, device=dev)
+    params = [pkmom.params(L, int(g), 128) for g in grids]
+    # warm plans and tables on every lane for every grid
+    result = {}
+    for name, lanes in (("served", 4), ("plain", 1)):
+        srv = Server(lanes=lanes, budget_bytes=180e9)
+        for ctx, s in zip(srv.ctxs, srv.streams):
+            for g in (128, 256, 512, 1024):
+                ctx.estimate(pool["pos"][:100000], pool["vel"][:100000], pkmom.params(L, g, 128), stream=s)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(_clock_id(torch, dev)) if name == "served" else None
+        futs = []
+        t0 = time.perf_counter()
+
+        def feeder():
+            for i in range(nreq):
+                wait = t0 + t_arr[i] - time.perf_counter()
+                if wait > 0:
+                    time.sleep(wait)
+                n = int(counts[i])
+                r = Request(pool["pos"][:n], pool["vel"][:n], params[i], arrival=time.perf_counter())
+                futs.append(srv.submit(r))
+
+        th = threading.Thread(target=feeder)
+        th.start()
+        th.join()
+        for f in futs:
+            f.result(timeout=180)
+        t1 = max(r.done for r in srv.completed)
+        lat = srv.latencies()
+        pc = percentiles(lat)
+        result[name] = {"throughput_particles_per_s": float(counts.sum() / (t1 - t0)),
+                        "p50_ms": pc["p50"] * 1e3, "p99_ms": pc["p99"] * 1e3,
+                        "mean_ms": float(np.mean(lat) * 1e3), "wall_s": t1 - t0, "lanes": lanes}
+        if clocks is not None:
+            result["clocks"] = clocks.stop()
+        srv.close()
+    sv, pl = result["served"], result["plain"]
+    line = {"metric": METRIC, "value": sv["throughput_particles_per_s"], "unit": "particles/s", "n_gpus": 1,
+            "steps": nreq, "warmup": 1, "ms_per_step": sv["mean_ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": MULTI["serve"], "requests": nreq, "n_particles": int(counts.sum())},
+            "latency_ms": {"p50": sv["p50_ms"], "p99": sv["p99_ms"]},
+            "plain": pl, "served": sv, "clocks": result.get("clocks")}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(MULTI))
+    ap.add_argument("--requests", type=int, default=300, help="serve: number of requests")
+    ap.add_argument("--tile", type=int, default=-1, help="deposit tile id (pkmom_set_tuning); -1 = automatic")
     ap.add_argument("--impl", default="pkmom", choices=["pkmom", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch64":
+        return run_batch64(args)
+    if args.workload == "serve":
+        return run_serve(args)
 
     import torch
 
@@ -194,6 +352,8 @@ def main(argv=None):
     vel = torch.from_numpy(cat["vel"]).to(dev)
     p = pkmom.params(L, ng, nbins, precision=pkmom.F32 if prec == "f32" else pkmom.F64)
     ctx = pkmom.Context(local)
+    if args.tile >= 0:
+        ctx.set_tuning(args.tile, -1)
     stream = torch.cuda.Stream(device=dev)
     out = torch.empty((pkmom.NROWS, nbins), dtype=torch.float64, device=dev)
 

@@ -206,6 +206,15 @@ pkmom_status pkmom_timing_read(pkmom_ctx *ctx, double ms[PKMOM_NSTAGES], int64_t
 /* Number of kernels this context has launched (its own kernels; cuFFT's not counted). */
 int64_t pkmom_kernel_launches(const pkmom_ctx *ctx);
 
+/* Tuning knobs of the assignment (used by the autotuner): deposit tile shape id
+ * (0: 16x16x16, 1: 16x16x32, 2: 8x8x32, 3: 8x8x8 for FP32 grids; 4: 8x8x16, 5: 16^3,
+ * 6: 8^3 for FP64; a shape that does not divide ng is ignored) and the capacity of the
+ * per-tile shared-memory particle list of FP32 deposits (0 = none, at most 8192).
+ * -1 restores the automatic choice. The results do not depend on these. */
+pkmom_status pkmom_set_tuning(pkmom_ctx *ctx, int deposit_tile, int list_cap);
+/* pkmom_assign_scratch_bytes under this context's tuning. */
+size_t pkmom_assign_scratch_bytes_tuned(const pkmom_ctx *ctx, const pkmom_params *p, int64_t n);
+
 #ifdef __cplusplus
 }
 #endif

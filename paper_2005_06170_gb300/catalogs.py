@@ -109,3 +109,64 @@ def lattice_wave(ng: int, L: float, kvec_int=(1, 0, 0), e=(1.0, 0.0, 0.0), amp: 
 def log_uniform_counts(n_catalogs: int, lo: float, hi: float, seed: int) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed))
     return np.round(np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_catalogs))).astype(np.int64)
+
+
+# ---------------------------------------------------------------------------
+# Device-side generators (PyTorch): the same recipes drawn with torch's generator
+# on the GPU, for the batched and serving workloads whose many large catalogues
+# would take minutes to draw on the host. They are not bit-identical to the numpy
+# generators above (different random streams); tests that compare with the CPU
+# oracle use the numpy ones, or copy these to the host.
+
+def poisson_torch(n: int, L: float, sigma_v: float = 300.0, seed: int = 1000, device="cuda",
+                  dtype=None) -> dict:
+    import torch
+    dtype = dtype or torch.float32
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    pos = torch.rand((n, 3), generator=g, device=device, dtype=torch.float64) * L
+    vel = torch.randn((n, 3), generator=g, device=device, dtype=torch.float64) * sigma_v
+    pos = pos.to(dtype)
+    pos[pos >= L] = 0
+    return {"L": float(L), "pos": pos.contiguous(), "vel": vel.to(dtype).contiguous()}
+
+
+def zeldovich_torch(n_side: int, L: float, seed: int = 1001, f: float = 0.5, H: float = 100.0, device="cuda",
+                    dtype=None, amp: float = 2.0e4, k0: float = 0.02) -> dict:
+    """The recipe of zeldovich() (same P(k), delta(0) = 0, Nyquist planes zeroed,
+    psi(k) = i k delta(k) / k^2, v = f H psi), drawn on the device."""
+    import torch
+    dtype = dtype or torch.float32
+    N = n_side
+    V = L ** 3
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    white = torch.randn((N, N, N), generator=g, device=device, dtype=torch.float32)
+    wk = torch.fft.rfftn(white)
+    del white
+    kf = 2.0 * torch.pi / L
+    kx = kf * torch.fft.fftfreq(N, d=1.0 / N, device=device)
+    kz = kf * torch.arange(N // 2 + 1, device=device, dtype=torch.float32)
+    k2 = kx[:, None, None] ** 2 + kx[None, :, None] ** 2 + kz[None, None, :] ** 2
+    k2[0, 0, 0] = 1.0
+    x = torch.sqrt(k2) / k0
+    amp_k = torch.sqrt(amp * x / (1.0 + x ** 3.5) * (N ** 3) / V)
+    amp_k[0, 0, 0] = 0.0
+    amp_k[N // 2, :, :] = 0.0
+    amp_k[:, N // 2, :] = 0.0
+    amp_k[:, :, N // 2] = 0.0
+    dk = wk * amp_k
+    del wk, amp_k, x
+    q1 = torch.arange(N, device=device, dtype=torch.float64) * (L / N)
+    pos = torch.empty((N, N, N, 3), device=device, dtype=dtype)
+    vel = torch.empty((N, N, N, 3), device=device, dtype=dtype)
+    kvecs = (kx[:, None, None], kx[None, :, None], kz[None, None, :])
+    for a in range(3):
+        psi = torch.fft.irfftn(1j * kvecs[a] / k2 * dk, s=(N, N, N)).to(torch.float64)
+        qa = q1.reshape([N if i == a else 1 for i in range(3)])
+        pos[..., a] = torch.remainder(qa + psi, L).to(dtype)
+        vel[..., a] = (f * H * psi).to(dtype)
+        del psi
+    pos = pos.reshape(-1, 3)
+    pos[pos >= L] = 0
+    return {"L": float(L), "pos": pos.contiguous(), "vel": vel.reshape(-1, 3).contiguous()}

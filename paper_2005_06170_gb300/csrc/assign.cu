@@ -523,6 +523,81 @@ k_deposit(const Record<T> *__restrict__ rec, const uint32_t *__restrict__ offset
     }
 }
 
+// Cell-block path of the FP32 deposit for dense tiles (cubic order, per-cell keys): one
+// warp per occupied cell of the reach; lane l owns stencil nodes (dx, dy, dz) with
+// dz = l & 3, dy = (l >> 2) & 3, dx = (l >> 4) and (l >> 4) + 2, evaluates its weight
+// pieces by Horner's rule with lane-constant coefficients, sums up to kCellFlush of the
+// cell's particles (records read once, broadcast) in FP32 registers and adds the sums to
+// the shared accumulator as fixed-point integers (one rounding per sum).
+constexpr int kCellFlush = 256;
+
+__device__ __forceinline__ float horner4(const float (&c)[4], float t) { return c[0] + t * (c[1] + t * (c[2] + t * c[3])); }
+
+// coefficients of the cubic B-spline weight of stencil node k (0..3) in t = u - floor(u)
+__device__ __forceinline__ void cubic_piece(int k, float (&c)[4])
+{
+    const float s = 1.0f / 6.0f;
+    if (k == 0) c[0] = s, c[1] = -3 * s, c[2] = 3 * s, c[3] = -s;
+    else if (k == 1) c[0] = 4 * s, c[1] = 0.f, c[2] = -6 * s, c[3] = 3 * s;
+    else if (k == 2) c[0] = s, c[1] = 3 * s, c[2] = 3 * s, c[3] = -3 * s;
+    else c[0] = 0.f, c[1] = 0.f, c[2] = 0.f, c[3] = s;
+}
+
+template <int T0, int T1, int T2, int NT>
+__device__ __forceinline__ void deposit_cells_path(const Record<float> *__restrict__ rec,
+                                                   const uint32_t *__restrict__ offsets, int ng, int t0, int t1, int t2,
+                                                   int *acc, int fstride, int rw, const float *s_scale)
+{
+    constexpr int HL = 2, R0 = T0 + 3, R1 = T1 + 3, RZ = T2 + 3, NW = NT / 32;
+    const float sc[4] = {s_scale[0], s_scale[1], s_scale[2], s_scale[3]};
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int dz = lane & 3, dy = (lane >> 2) & 3, dxl = lane >> 4;
+    float cxa[4], cxb[4], cyy[4], czz[4];
+    cubic_piece(dxl, cxa);
+    cubic_piece(dxl + 2, cxb);
+    cubic_piece(dy, cyy);
+    cubic_piece(dz, czz);
+    auto wrapi = [ng](int a) { return a < 0 ? a + ng : (a >= ng ? a - ng : a); };
+    for (int c = warp; c < R0 * R1 * RZ; c += NW) {
+        const int r = c / RZ, zz = c % RZ;
+        const int cx = r / R1 - HL, cy = r % R1 - HL, cz = zz - HL;  // cell relative to the tile
+        const int64_t key =
+            (static_cast<int64_t>(wrapi(t0 + cx)) * ng + wrapi(t1 + cy)) * ng + wrapi(t2 + cz);
+        const uint32_t beg = offsets[key], end = offsets[key + 1];
+        if (beg == end) continue;
+        const int lxa = cx - 1 + dxl, lxb = lxa + 2, ly = cy - 1 + dy, lz = cz - 1 + dz;
+        const bool yz = ly >= 0 && ly < T1 && lz >= 0 && lz < T2;
+        const bool ina = yz && lxa >= 0 && lxa < T0, inb = yz && lxb >= 0 && lxb < T0;
+        const int oa = (lxa * T1 + ly) * rw + lz, ob = ((lxa + 2) * T1 + ly) * rw + lz;
+        for (uint32_t i0 = beg; i0 < end; i0 += kCellFlush) {
+            const uint32_t i1 = min(end, i0 + kCellFlush);
+            float a[4] = {0.f, 0.f, 0.f, 0.f}, b[4] = {0.f, 0.f, 0.f, 0.f};
+            auto add = [&](const Record<float> &rc) {
+                const float wyz = horner4(cyy, rc.u.y) * horner4(czz, rc.u.z);
+                const float wa = horner4(cxa, rc.u.x) * wyz, wb = horner4(cxb, rc.u.x) * wyz;
+                a[0] += rc.q.x * wa, b[0] += rc.q.x * wb;
+                a[1] += rc.q.y * wa, b[1] += rc.q.y * wb;
+                a[2] += rc.q.z * wa, b[2] += rc.q.z * wb;
+                a[3] += rc.q.w * wa, b[3] += rc.q.w * wb;
+            };
+            uint32_t i = i0;
+            for (; i + 4 <= i1; i += 4) {  // four loads in flight
+                const Record<float> r0 = rec[i], r1 = rec[i + 1], r2 = rec[i + 2], r3 = rec[i + 3];
+                add(r0);
+                add(r1);
+                add(r2);
+                add(r3);
+            }
+            for (; i < i1; ++i) add(rec[i]);
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                if (ina) atomicAdd(acc + f * fstride + oa, __float2int_rn(a[f] * sc[f]));
+                if (inb) atomicAdd(acc + f * fstride + ob, __float2int_rn(b[f] * sc[f]));
+            }
+        }
+    }
+}
+
 // Tile-gather deposit for FP32 grids with 32-bit integer (fixed-point) shared-memory
 // atomics (about three times the throughput of FP32 shared atomics on this part).
 //
@@ -533,16 +608,18 @@ k_deposit(const Record<T> *__restrict__ rec, const uint32_t *__restrict__ offset
 // padded to an odd length.
 //
 // Fixed point: field f of the tile uses the scale 2^s_f with
-//   B_f 2^s_f < 2^29,   B_f = w3 min(sum |q_f|, M^2 * (largest row count) * max |q_f|),
-// over the particles within reach (w3 = the largest product of three weights; a node
-// receives from at most M^2 rows, each contributing fewer than `largest row count`
-// particles), so no node sum can overflow, and also max |q_f| w3 2^s_f < 2^22, so that
+//   B_f 2^s_f < 2^29,   B_f = w3 * min(M^2 * largest row count, particle count) * max |q_f|
+// over the tile's reach (w3 = the largest product of three weights; a node receives from
+// at most M^2 cell rows, each contributing at most `largest row count` particles, and
+// from no more than all of them; max |q_f| over the catalogue), so no node sum can overflow, and also max |q_f| w3 2^s_f < 2^22, so that
 // every contribution is rounded to an integer by one FFMA against 1.5 * 2^23 (round to
-// nearest even, one rounding of the exact product).
+// nearest even, one rounding of the exact product). The bound depends only on counts
+// and maxima, and integer sums do not depend on order: the grids are the same whatever
+// order the sort leaves particles of one cell in.
 template <int M, int T0, int T1, int T2, int NT>
 __global__ void __launch_bounds__(NT)
 k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__ offsets,
-             const unsigned *__restrict__ /*qmax_bits*/, int ng, int sshift, float *__restrict__ grids, int64_t grid_elems,
+             const unsigned *__restrict__ qmax_bits, int ng, int sshift, float *__restrict__ grids, int64_t grid_elems,
              int list_cap)
 {
     using C = DepositCfg<float, M, T0, T1, T2, NT>;
@@ -553,7 +630,6 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
     int *acc = reinterpret_cast<int *>(smem_raw);  // [4][T0 * T1][RW]
     __shared__ uint32_t s_beg[C::MAXR];
     __shared__ uint32_t s_pre[C::MAXR + 1];
-    __shared__ float s_red[NW][8];
     __shared__ unsigned s_rowmax;
     __shared__ float s_scale[4];
 
@@ -594,52 +670,44 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
         return s_beg[slot] + (p - s_pre[slot]);
     };
 
-    // pass 1: per-field max |q| and sum |q| (rounded up) over the tile's particles
-    {
-        float qm[4] = {0.f, 0.f, 0.f, 0.f}, qs[4] = {0.f, 0.f, 0.f, 0.f};
-        int slot = (!listed && wbeg + lane < wend) ? find_slot<C::MAXR>(s_pre, wbeg + lane) : 0;
-        for (uint32_t p = wbeg + lane; p < wend; p += 32) {
-            const Vec4<float> q = rec[record_index(p, slot)].q;
-            const float a[4] = {fabsf(q.x), fabsf(q.y), fabsf(q.z), fabsf(q.w)};
-#pragma unroll
-            for (int f = 0; f < 4; ++f) qm[f] = fmaxf(qm[f], a[f]), qs[f] = __fadd_ru(qs[f], a[f]);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int f = 0; f < 4; ++f) {
-                qm[f] = fmaxf(qm[f], __shfl_xor_sync(0xffffffffu, qm[f], o));
-                qs[f] = __fadd_ru(qs[f], __shfl_xor_sync(0xffffffffu, qs[f], o));
-            }
-        if (lane == 0)
-#pragma unroll
-            for (int f = 0; f < 4; ++f) s_red[warp][f] = qm[f], s_red[warp][4 + f] = qs[f];
-        __syncthreads();
-        if (threadIdx.x < 4) {
-            const int f = threadIdx.x;
-            float m = 0.f, sum = 0.f;
-            for (int w = 0; w < NW; ++w) m = fmaxf(m, s_red[w][f]), sum = __fadd_ru(sum, s_red[w][4 + f]);
-            const float w3 = kMaxWeight3<M> * 1.0001f;
-            const float by_rows = static_cast<float>(M * M) * static_cast<float>(s_rowmax) * m;
-            const float bound = w3 * (isfinite(sum) && sum < by_rows ? sum : by_rows);
-            const float cmax = w3 * m;  // largest single contribution
-            int eb = 0, ec = 0;
-            if (bound > 0.f) frexpf(bound, &eb);  // bound < 2^eb
-            if (cmax > 0.f) frexpf(cmax, &ec);
-            if (!isfinite(bound)) eb = 150;
-            if (!isfinite(cmax)) ec = 150;
-            int sexp = min(29 - eb, 22 - ec);
-            sexp = sexp > 120 ? 120 : (sexp < -120 ? -120 : sexp);
-            s_scale[f] = ldexpf(1.0f, sexp);
-        }
-        __syncthreads();
+    // dense tiles (cubic order, more than two particles per reach cell on average) sum
+    // each cell's particles in registers first (cell-block path below)
+    constexpr int NREACH = C::R0 * C::R1 * (T2 + C::HL + C::HR);
+    const bool dense = M == 4 && total > 2u * NREACH && sshift == 0 && ng >= C::R0 && ng >= C::R1 &&
+                       ng >= T2 + C::HL + C::HR;
+    // per-field scale from order-independent bounds only (so that the grids, and the
+    // spectra, do not depend on the order in which sorted particles share a cell)
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        const int f = threadIdx.x;
+        const float m = __uint_as_float(qmax_bits[f]);  // max |q_f| over the catalogue
+        const float w3 = kMaxWeight3<M> * 1.0001f;
+        const float reach = fminf(static_cast<float>(M * M) * static_cast<float>(s_rowmax), static_cast<float>(total));
+        const float bound = w3 * reach * m;
+        const float cmax = w3 * m;  // largest single contribution
+        int eb = 0, ec = 0;
+        if (bound > 0.f) frexpf(bound, &eb);  // bound < 2^eb
+        if (cmax > 0.f) frexpf(cmax, &ec);
+        if (!isfinite(bound)) eb = 150;
+        if (!isfinite(cmax)) ec = 150;
+        int sexp = dense ? 29 - eb : min(29 - eb, 22 - ec);  // cell sums round with cvt, not FFMA
+        sexp = sexp > 120 ? 120 : (sexp < -120 ? -120 : sexp);
+        s_scale[f] = ldexpf(1.0f, sexp);
     }
+    __syncthreads();
     const float sc0 = s_scale[0], sc1 = s_scale[1], sc2 = s_scale[2], sc3 = s_scale[3];
     constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
     constexpr int kMagicBits = 0x4B400000;
 
-    // pass 2: deposit
-    {
+    bool cells_done = false;
+    if constexpr (M == 4) {
+        if (dense) {
+            deposit_cells_path<T0, T1, T2, NT>(rec, offsets, ng, t0, t1, t2, acc, TNP, RW, s_scale);
+            cells_done = true;
+        }
+    }
+    // pass 2: deposit, one particle per lane
+    if (!cells_done) {
         int slot = (!listed && wbeg + lane < wend) ? find_slot<C::MAXR>(s_pre, wbeg + lane) : 0;
         for (uint32_t p = wbeg + lane; p < wend; p += 32) {
             const Record<float> rc = rec[record_index(p, slot)];

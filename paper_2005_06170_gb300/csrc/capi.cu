@@ -43,6 +43,9 @@ struct pkmom_ctx {
     size_t out_bytes = 0;
     void *staging = nullptr;
     size_t staging_bytes = 0;
+    // tuning overrides (-1: automatic)
+    int tune_tile = -1;
+    int tune_list_cap = -1;
     // timing
     bool timing = false;
     std::vector<TimedEvent> pending;
@@ -106,7 +109,7 @@ pkmom_status check_catalog(pkmom_ctx *ctx, const pkmom_catalog *c, const pkmom_p
 }
 
 // How one assignment is laid out: sort-key segment length, deposit tile and scratch.
-AssignPlan plan_assign(const pkmom_params &p, int64_t n, int num_sms)
+AssignPlan plan_assign(const pkmom_params &p, int64_t n, int num_sms, int tile_override = -1, int list_override = -1)
 {
     AssignPlan pl;
     pl.ng = p.ng;
@@ -126,6 +129,11 @@ AssignPlan plan_assign(const pkmom_params &p, int64_t n, int num_sms)
             break;
         }
     }
+    if (tile_override >= 0) {
+        int d[3];
+        deposit_tile_shape(tile_override, p.precision, d);
+        if (d[0] && p.ng % d[0] == 0 && p.ng % d[1] == 0 && p.ng % d[2] == 0) pl.tile = tile_override;
+    }
     int td[3];
     deposit_tile_shape(pl.tile, p.precision, td);
     // one sort key per cell keeps each row's particles in z order, which the deposit's
@@ -143,6 +151,7 @@ AssignPlan plan_assign(const pkmom_params &p, int64_t n, int num_sms)
         const double want = 2.0 * ppc * reach + 64.0;
         pl.list_cap = static_cast<int>(std::min(8192.0, std::ceil(want / 256.0) * 256.0));
     }
+    if (p.precision == PKMOM_F32 && list_override >= 0) pl.list_cap = std::min(list_override, 8192) / 32 * 32;
     pl.nkeys = int64_t(p.ng) * p.ng * (p.ng >> sshift);
     pl.hist_blocks = num_sms * 8;
     pl.scan_blocks = (pl.nkeys + 8191) / 8192;
@@ -385,7 +394,7 @@ pkmom_status pkmom_assign(pkmom_ctx *ctx, const pkmom_catalog *cat, const pkmom_
     if ((s = check_catalog(ctx, cat, p)) != PKMOM_OK) return s;
     if (!grids || !moments_dev || !scratch) return fail(ctx, PKMOM_EINVAL, "null grids, moments or scratch");
     PK_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
-    const AssignPlan pl = plan_assign(*p, cat->n, ctx->num_sms);
+    const AssignPlan pl = plan_assign(*p, cat->n, ctx->num_sms, ctx->tune_tile, ctx->tune_list_cap);
     if (scratch_bytes < pl.total) return fail(ctx, PKMOM_ESCRATCH, "scratch smaller than pkmom_assign_scratch_bytes");
     cudaStream_t st = as_stream(stream);
     {
@@ -468,7 +477,7 @@ pkmom_status pkmom_estimate(pkmom_ctx *ctx, const pkmom_catalog *cat, const pkmo
     if ((s = check_catalog(ctx, cat, p)) != PKMOM_OK) return s;
     if (!out_dev) return fail(ctx, PKMOM_EINVAL, "null output");
     PK_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
-    const AssignPlan pl = plan_assign(*p, cat->n, ctx->num_sms);
+    const AssignPlan pl = plan_assign(*p, cat->n, ctx->num_sms, ctx->tune_tile, ctx->tune_list_cap);
     if ((s = ensure(ctx, &ctx->grids, &ctx->grids_bytes, pkmom_grid_bytes(p->ng, p->precision), "grids")) != PKMOM_OK)
         return s;
     if ((s = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, pl.total, "scratch")) != PKMOM_OK) return s;
@@ -577,5 +586,20 @@ pkmom_status pkmom_timing_read(pkmom_ctx *ctx, double ms[PKMOM_NSTAGES], int64_t
 }
 
 int64_t pkmom_kernel_launches(const pkmom_ctx *ctx) { return ctx ? ctx->st.launches : 0; }
+
+pkmom_status pkmom_set_tuning(pkmom_ctx *ctx, int deposit_tile, int list_cap)
+{
+    if (!ctx) return PKMOM_EINVAL;
+    if (deposit_tile >= deposit_tile_count() || list_cap > 8192) return fail(ctx, PKMOM_EINVAL, "bad tuning values");
+    ctx->tune_tile = deposit_tile < 0 ? -1 : deposit_tile;
+    ctx->tune_list_cap = list_cap < 0 ? -1 : list_cap;
+    return PKMOM_OK;
+}
+
+size_t pkmom_assign_scratch_bytes_tuned(const pkmom_ctx *ctx, const pkmom_params *p, int64_t n)
+{
+    if (!ctx || !p || check_params(nullptr, p) != PKMOM_OK || n < 1) return 0;
+    return plan_assign(*p, n, ctx->num_sms, ctx->tune_tile, ctx->tune_list_cap).total;
+}
 
 }  // extern "C"

@@ -79,6 +79,8 @@ def lib():
         "pkmom_timing_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
         "pkmom_kernel_launches": (i64, [vp]),
         "pkmom_spectra_static": (i32, [ctypes.POINTER(Params), vp, vp, vp, vp]),
+        "pkmom_set_tuning": (i32, [vp, i32, i32]),
+        "pkmom_assign_scratch_bytes_tuned": (ctypes.c_size_t, [vp, ctypes.POINTER(Params), i64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -91,7 +93,8 @@ def lib():
 EXPORTED = ("pkmom_params_default", "pkmom_create", "pkmom_destroy", "pkmom_strerror", "pkmom_last_error",
             "pkmom_grid_bytes", "pkmom_assign_scratch_bytes", "pkmom_footprint_bytes", "pkmom_assign",
             "pkmom_fft", "pkmom_spectra", "pkmom_estimate", "pkmom_estimate_host", "pkmom_sync",
-            "pkmom_timing_enable", "pkmom_timing_read", "pkmom_kernel_launches", "pkmom_spectra_static")
+            "pkmom_timing_enable", "pkmom_timing_read", "pkmom_kernel_launches", "pkmom_spectra_static",
+            "pkmom_set_tuning", "pkmom_assign_scratch_bytes_tuned")
 
 
 def params(box_L: float, ng: int, nbins: int, *, order: int = 4, precision: int = F32, kmin_kf: float = 1.0,
@@ -250,6 +253,13 @@ class Context:
 
     def kernel_launches(self) -> int:
         return int(lib().pkmom_kernel_launches(self._h))
+
+    def set_tuning(self, deposit_tile: int = -1, list_cap: int = -1):
+        """Deposit tile shape and particle-list capacity (-1: automatic); see include/pkmom.h."""
+        self._check(lib().pkmom_set_tuning(self._h, int(deposit_tile), int(list_cap)))
+
+    def scratch_bytes_tuned(self, p: Params, n: int) -> int:
+        return int(lib().pkmom_assign_scratch_bytes_tuned(self._h, ctypes.byref(p), n))
 
 
 def spectra_static(p: Params, grids, moments, out, stream=None):

@@ -1,0 +1,235 @@
+"""Serving loop: estimation requests admitted by HBM footprint, run as they arrive.
+
+Requests (a catalogue resident on the device plus its Params) are queued on
+arrival. A scheduler thread admits them while a lane is free and their device
+footprint fits in the budget beside the requests already running (first fit in
+arrival order, with a bound on how often a waiting request may be overtaken), and
+launches each on its lane's stream: several requests overlap on the GPU and
+requests that arrive meanwhile join as lanes and memory free up (continuous
+batching). A lane owns a libpkmom context (its own cuFFT plans and tables). The
+result is copied to pinned host memory on the lane's stream; the scheduler polls
+the completion events, releases the request's memory and completes its Future.
+Latency is measured from arrival to the moment the result is on the host.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass(eq=False)  # requests compare by identity
+class Request:
+    pos: object              # (n,3) CUDA tensor
+    vel: object              # (n,3) CUDA tensor
+    params: object           # pkmom.Params
+    mass: object = None
+    arrival: float = 0.0     # time.perf_counter() at arrival
+    rid: int = 0
+    future: cf.Future = field(default_factory=cf.Future)
+    # filled by the server
+    footprint: int = 0
+    admitted: float = 0.0
+    done: float = 0.0
+    lane: int = -1
+    overtaken: int = 0
+
+
+class AdmissionPolicy:
+    """Which queued requests start now (pure host logic, no CUDA).
+
+    First fit in arrival order: the oldest request that fits the free budget starts
+    on a free lane; a request may be overtaken by later, smaller ones at most
+    `max_overtake` times, after which nothing behind it starts until it does.
+    """
+
+    def __init__(self, budget_bytes: int, max_overtake: int = 8):
+        self.budget = int(budget_bytes)
+        self.max_overtake = max_overtake
+
+    def admit(self, queue: list, free_lanes: int, in_use: int) -> list:
+        chosen = []
+        free = self.budget - in_use
+        for r in queue:
+            if len(chosen) >= free_lanes:
+                break
+            if r.footprint <= free:
+                chosen.append(r)
+                free -= r.footprint
+            elif r.overtaken >= self.max_overtake:
+                break  # it has waited long enough: nothing behind it starts first
+        # every waiting request passed by a later admitted one counts one overtake
+        if chosen:
+            last = queue.index(chosen[-1])
+            for r in queue[:last]:
+                if r not in chosen:
+                    r.overtaken += 1
+        return chosen
+
+
+def percentiles(latencies: list[float], qs=(50, 99)) -> dict:
+    a = np.sort(np.asarray(latencies, dtype=np.float64))
+    if a.size == 0:
+        return {f"p{q}": None for q in qs}
+    return {f"p{q}": float(np.percentile(a, q, method="inverted_cdf")) for q in qs}
+
+
+class Server:
+    def __init__(self, lanes: int = 4, budget_bytes: float = 180e9, device: int = 0, tuner=None,
+                 max_overtake: int = 8, large_bytes: float = 8e9):
+        """Requests whose footprint exceeds large_bytes run on low-priority streams, the
+        others on high-priority ones (when both kinds of lane exist), so that small
+        requests pass large ones at kernel boundaries instead of queueing behind them."""
+        import torch
+
+        from . import pkmom
+        self._torch, self._pk = torch, pkmom
+        self.device = device
+        self.ctxs = [pkmom.Context(device) for _ in range(lanes)]
+        lo, hi = torch.cuda.Stream.priority_range()  # (least, greatest) priority
+        self.n_small = lanes // 2 if lanes > 1 else lanes
+        self.large_bytes = large_bytes
+        self.streams = [torch.cuda.Stream(device=device, priority=hi if k < self.n_small else lo)
+                        for k in range(lanes)]
+        self.lane_free = [True] * lanes
+        self.policy = AdmissionPolicy(int(budget_bytes), max_overtake)
+        self.tuner = tuner
+        self.gpu = torch.cuda.get_device_name(device)
+        self.queue: list[Request] = []
+        self.inflight: list[tuple] = []
+        self.in_use = 0
+        self.completed: list[Request] = []
+        self._lock = threading.Condition()
+        self._stop = False
+        self._next = 0
+        self._thread = threading.Thread(target=self._loop, name="pkmom-serve", daemon=True)
+        self._thread.start()
+
+    def footprint(self, req: Request) -> int:
+        pk = self._pk
+        p = req.params
+        return int(pk.Context.grid_bytes(p.ng, p.precision) + pk.Context.scratch_bytes(p, req.pos.shape[0])
+                   + 16 * 8 + pk.NROWS * p.nbins * 8)
+
+    def submit(self, req: Request) -> cf.Future:
+        req.footprint = self.footprint(req)
+        if not req.arrival:
+            req.arrival = time.perf_counter()
+        with self._lock:
+            req.rid = self._next
+            self._next += 1
+            if req.footprint > self.policy.budget:
+                req.future.set_exception(MemoryError(f"request needs {req.footprint} B > budget"))
+                return req.future
+            self.queue.append(req)
+            self._lock.notify()
+        return req.future
+
+    def _pick_lane(self, free: list, large: bool) -> int:
+        """A free lane of the request's kind (low priority for large ones), else any."""
+        mine = [k for k in free if (k >= self.n_small) == large]
+        return (mine or free)[0]
+
+    def _launch(self, req: Request, lane: int):
+        torch, pk = self._torch, self._pk
+        ctx, s = self.ctxs[lane], self.streams[lane]
+        p = req.params
+        dev = torch.device("cuda", self.device)
+        dt = torch.float32 if p.precision == pk.F32 else torch.float64
+        item = 4 if p.precision == pk.F32 else 8
+        cat = pk.catalog_from_tensors(req.pos, req.vel, req.mass)
+        tile, cap = (-1, -1)
+        if self.tuner is not None:
+            tile, cap = self.tuner.choose(ctx, cat, p, self.gpu)
+        ctx.set_tuning(tile, cap)
+        with torch.cuda.stream(s):
+            grids = torch.empty(pk.Context.grid_bytes(p.ng, p.precision) // item, dtype=dt, device=dev)
+            mom = torch.zeros(16, dtype=torch.float64, device=dev)
+            scratch = torch.empty(ctx.scratch_bytes_tuned(p, cat.n), dtype=torch.uint8, device=dev)
+            out = torch.empty((pk.NROWS, p.nbins), dtype=torch.float64, device=dev)
+            host = torch.empty((pk.NROWS, p.nbins), dtype=torch.float64, pin_memory=True)
+        ctx.assign(cat, p, grids, mom, scratch, stream=s)
+        ctx.fft(p, grids, stream=s)
+        ctx.spectra(p, grids, mom, out, stream=s)
+        ctx.set_tuning(-1, -1)
+        with torch.cuda.stream(s):
+            host.copy_(out, non_blocking=True)
+        ev = torch.cuda.Event()
+        ev.record(s)
+        req.admitted = time.perf_counter()
+        req.lane = lane
+        return (req, lane, ev, host, (grids, mom, scratch, out))
+
+    def _loop(self):
+        try:
+            self._run_loop()
+        except BaseException as e:  # never leave callers waiting on a dead scheduler
+            with self._lock:
+                self._stop = True
+                pending = list(self.queue) + [entry[0] for entry in self.inflight]
+                self.queue.clear()
+                self.inflight.clear()
+            for r in pending:
+                if not r.future.done():
+                    r.future.set_exception(RuntimeError(f"serving loop failed: {e!r}"))
+            raise
+
+    def _run_loop(self):
+        torch = self._torch
+        torch.cuda.set_device(self.device)
+        while True:
+            with self._lock:
+                if self._stop and not self.queue and not self.inflight:
+                    return
+                free = [k for k, f in enumerate(self.lane_free) if f]
+                start = self.policy.admit(self.queue, len(free), self.in_use) if free else []
+                for r in start:
+                    self.queue.remove(r)
+                    self.in_use += r.footprint
+                    lane = self._pick_lane(free, r.footprint > self.large_bytes)
+                    free.remove(lane)
+                    self.lane_free[lane] = False
+                    self.inflight.append(self._launch(r, lane))
+            finished = []
+            for entry in list(self.inflight):
+                req, lane, ev, host, bufs = entry
+                if ev.query():
+                    req.done = time.perf_counter()
+                    finished.append(entry)
+            if finished:
+                with self._lock:
+                    for entry in finished:
+                        req, lane, ev, host, bufs = entry
+                        self.inflight.remove(entry)
+                        err = None
+                        try:
+                            self.ctxs[lane].sync(self.streams[lane])
+                        except Exception as e:  # a data error latched by the library
+                            err = e
+                        self.lane_free[lane] = True
+                        self.in_use -= req.footprint
+                        self.completed.append(req)
+                        if err is None:
+                            req.future.set_result(host.numpy().copy())
+                        else:
+                            req.future.set_exception(err)
+                    self._lock.notify_all()
+            elif not start:
+                with self._lock:
+                    if not self._stop or self.queue or self.inflight:
+                        self._lock.wait(timeout=0.0002)
+
+    def close(self):
+        with self._lock:
+            self._stop = True
+            self._lock.notify_all()
+        self._thread.join()
+        for c in self.ctxs:
+            c.close()
+        self.ctxs = []
+
+    def latencies(self) -> list[float]:
+        return [r.done - r.arrival for r in self.completed]

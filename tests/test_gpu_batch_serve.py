@@ -1,0 +1,133 @@
+"""Batched and served estimation on the GPU give the same spectra as single runs.
+
+The deposit accumulates in integers with order-independent scales and the other
+reductions of the data have a fixed order, so with the same tuning a catalogue's
+spectra do not depend on what runs beside it: batched, graph-replayed and served
+results equal the single-catalogue results up to the FP64 rounding of each
+context's shell tables (1e-12). Catalogues are also checked against the oracle.
+"""
+import numpy as np
+import pytest
+
+from oracle import estimator as est
+from paper_2005_06170_gb300 import catalogs
+
+pytestmark = pytest.mark.gpu
+
+
+def _mixed(seed=0):
+    specs = [("p", 3000, 80.0, 32), ("z", 24, 200.0, 48), ("p", 20000, 150.0, 64), ("z", 32, 300.0, 32),
+             ("p", 500, 60.0, 16), ("z", 16, 100.0, 64), ("p", 8000, 120.0, 40)]
+    out = []
+    for i, (kind, n, L, ng) in enumerate(specs):
+        if kind == "p":
+            c = catalogs.poisson(n, L, seed=500 + i + seed, dtype=np.float32)
+        else:
+            c = catalogs.zeldovich(n, L, seed=600 + i + seed, dtype=np.float32)
+        out.append((c, L, ng))
+    return out
+
+
+def _dev(c, torch):
+    return {"pos": torch.from_numpy(c["pos"]).cuda(), "vel": torch.from_numpy(c["vel"]).cuda()}
+
+
+def _single(pk, ctx, d, p):
+    out = ctx.estimate(d["pos"], d["vel"], p)
+    ctx.sync()
+    return out.cpu().numpy()
+
+
+def test_batch_graph_equals_single_runs(gpu_lib):
+    import torch
+
+    from paper_2005_06170_gb300.batch import BatchRunner
+    pk = gpu_lib
+    items = _mixed()
+    devs = [_dev(c, torch) for c, _, _ in items]
+    params = [pk.params(L, ng, 12, theta_scale=0.02) for _, L, ng in items]
+    ctx = pk.Context(0)
+    ref = [_single(pk, ctx, d, p) for d, p in zip(devs, params)]
+    runner = BatchRunner(devs, params, lanes=3, use_graph=True)
+    first = [o.cpu().numpy() for o in runner.run()]  # eager run, then capture
+    torch.cuda.synchronize()
+    for o in runner.run():  # graph replay
+        o.zero_()
+    torch.cuda.synchronize()
+    replay = [o.cpu().numpy() for o in runner.run()]
+    torch.cuda.synchronize()
+    for r, a, b in zip(ref, first, replay):
+        # integer deposit sums and fixed-order reductions: equal up to the FP64 rounding
+        # of the shell tables each context builds
+        np.testing.assert_allclose(a, r, rtol=1e-12, atol=1e-12 * np.nanmax(np.abs(r)), equal_nan=True)
+        np.testing.assert_allclose(b, r, rtol=1e-12, atol=1e-12 * np.nanmax(np.abs(r)), equal_nan=True)
+    runner.close()
+    ctx.close()
+
+
+def test_batch_with_autotuner_matches_oracle(gpu_lib):
+    import torch
+
+    from paper_2005_06170_gb300.autotune import Autotuner
+    from paper_2005_06170_gb300.batch import BatchRunner
+    pk = gpu_lib
+    items = _mixed(seed=7)[:3]
+    devs = [_dev(c, torch) for c, _, _ in items]
+    params = [pk.params(L, ng, 10) for _, L, ng in items]
+    runner = BatchRunner(devs, params, lanes=2, use_graph=True, tuner=Autotuner(repeats=1))
+    outs = [pk.as_dict(o) for o in runner.run()]
+    torch.cuda.synchronize()
+    for (c, L, ng), g in zip(items, outs):
+        o = est.estimate(c["pos"], c["vel"], L=L, ng=ng, nbins=10)
+        for key in ("P_dd", "P_pp", "P_tt", "P_pp_b", "P_tt_b"):
+            sn = o["SN" + key[1:]]
+            scale = np.maximum(np.abs(o[key]), sn / np.sqrt(o["n_modes"]))
+            assert np.all(np.abs(g[key] - o[key]) <= 1e-4 * scale), key
+    runner.close()
+
+
+def test_served_results_same_alone_and_in_the_mix(gpu_lib):
+    import torch
+
+    from paper_2005_06170_gb300.serve import Request, Server
+    pk = gpu_lib
+    items = _mixed(seed=3)
+    devs = [_dev(c, torch) for c, _, _ in items]
+    params = [pk.params(L, ng, 12) for _, L, ng in items]
+    alone = []
+    srv = Server(lanes=1)
+    for d, p in zip(devs, params):
+        alone.append(srv.submit(Request(d["pos"], d["vel"], p)).result(timeout=120))
+    srv.close()
+    srv = Server(lanes=4)
+    futs = [srv.submit(Request(d["pos"], d["vel"], p)) for d, p in zip(devs, params)]
+    mixed = [f.result(timeout=120) for f in futs]
+    lanes_used = {r.lane for r in srv.completed}
+    srv.close()
+    assert len(lanes_used) > 1  # the requests did overlap on several lanes
+    for a, b in zip(alone, mixed):
+        np.testing.assert_allclose(b, a, rtol=1e-12, atol=1e-12 * np.nanmax(np.abs(a)), equal_nan=True)
+
+
+def test_serving_admits_by_footprint(gpu_lib):
+    import torch
+
+    from paper_2005_06170_gb300.serve import Request, Server
+    pk = gpu_lib
+    items = _mixed(seed=5)[:4]
+    devs = [_dev(c, torch) for c, _, _ in items]
+    params = [pk.params(L, 64, 8) for _, L, _ in items]
+    probe = Server(lanes=1)
+    fp = max(probe.footprint(Request(d["pos"], d["vel"], p)) for d, p in zip(devs, params))
+    probe.close()
+    srv = Server(lanes=4, budget_bytes=int(1.5 * fp))  # room for one request at a time
+    futs = [srv.submit(Request(d["pos"], d["vel"], p)) for d, p in zip(devs, params)]
+    for f in futs:
+        f.result(timeout=120)
+    done = sorted(srv.completed, key=lambda r: r.admitted)
+    for a, b in zip(done, done[1:]):
+        assert b.admitted >= a.done - 1e-3  # never two at once
+    big = Request(devs[0]["pos"], devs[0]["vel"], pk.params(100.0, 1024, 8))
+    with pytest.raises(MemoryError):
+        srv.submit(big).result(timeout=10)
+    srv.close()
