@@ -15,8 +15,9 @@ import threading
 
 # deposit tile shapes of the library (x, y, z nodes), by tile id
 TILES = {0: (16, 16, 16), 1: (16, 16, 32), 2: (8, 8, 32), 3: (8, 8, 8),
-         4: (8, 8, 16), 5: (16, 16, 16), 6: (8, 8, 8)}
-F32_TILES = (0, 1, 2, 3)
+         4: (8, 8, 16), 5: (16, 16, 16), 6: (8, 8, 8), 7: (16, 16, 16)}
+F32_TILES = (0, 1, 2, 3, 7)
+HOME_TILE = 7  # each particle deposited once by the tile owning its cell (no list)
 F64_TILES = (4, 5, 6)
 
 
@@ -34,7 +35,7 @@ def candidates(ng: int, precision: int) -> list[tuple[int, int]]:
         d = TILES[t]
         if all(ng % x == 0 for x in d):
             out.append((t, -1))
-            if precision == 0:
+            if precision == 0 and t != HOME_TILE:
                 out.append((t, 0))
     return out
 

@@ -543,20 +543,88 @@ __device__ __forceinline__ void cubic_piece(int k, float (&c)[4])
     else c[0] = 0.f, c[1] = 0.f, c[2] = 0.f, c[3] = s;
 }
 
+__device__ __forceinline__ int round_shift(int v, int d) { return d > 0 ? (v + (1 << (d - 1))) >> d : v; }
+
+// Weight pieces of a lane's two stencil nodes (dx, dx + 2; dy; dz) in the cell-block paths.
+struct CellPieces {
+    float xa[4], xb[4], y[4], z[4];
+};
+
+// Sums of one chunk (at most kCellFlush particles) of a cell for a lane's two stencil
+// nodes. Each contribution is rounded once to the fine scale 2^sf (below 2^22 in
+// magnitude: one FFMA against 1.5 * 2^23) and added as an integer; the chunk sum is then
+// rounded to the tile scale by a right shift of sf - st bits. Integer sums: the result
+// does not depend on the order in which the sort left the cell's particles.
+template <int F0 = 0, int NF = 4>
+__device__ __forceinline__ void cell_chunk(const Record<float> *__restrict__ rec, uint32_t i0, uint32_t i1,
+                                           const CellPieces &pc, const float (&fine)[4], const int (&shift)[4],
+                                           int (&a)[NF], int (&b)[NF])
+{
+    constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+    constexpr int kMagicBits = 0x4B400000;
+    int sa[NF], sb[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) sa[f] = 0, sb[f] = 0;
+    auto add = [&](const Record<float> &rc) {
+        const float wyz = horner4(pc.y, rc.u.y) * horner4(pc.z, rc.u.z);
+        const float wa = horner4(pc.xa, rc.u.x) * wyz, wb = horner4(pc.xb, rc.u.x) * wyz;
+        const float qv[4] = {rc.q.x, rc.q.y, rc.q.z, rc.q.w};
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const float q = qv[F0 + f] * fine[F0 + f];
+            sa[f] += __float_as_int(fmaf(q, wa, kMagic)) - kMagicBits;
+            sb[f] += __float_as_int(fmaf(q, wb, kMagic)) - kMagicBits;
+        }
+    };
+    uint32_t i = i0;
+    for (; i + 4 <= i1; i += 4) {  // four loads in flight
+        const Record<float> r0 = rec[i], r1 = rec[i + 1], r2 = rec[i + 2], r3 = rec[i + 3];
+        add(r0);
+        add(r1);
+        add(r2);
+        add(r3);
+    }
+    for (; i < i1; ++i) add(rec[i]);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        a[f] = round_shift(sa[f], shift[F0 + f]);
+        b[f] = round_shift(sb[f], shift[F0 + f]);
+    }
+}
+
+// Fixed-point scales of a tile: 2^st with (bound of any node sum) * 2^st < 2^29, and,
+// for the cell-block paths, the fine scale 2^sf with (largest contribution) * 2^sf < 2^22
+// and st <= sf. Per-particle paths round at 2^min(st, sf) directly.
+__device__ __forceinline__ void tile_scales(float bound, float cmax, bool cells, float &scale, float &fine, int &shift)
+{
+    int eb = 0, ec = 0;
+    if (bound > 0.f) frexpf(bound, &eb);  // bound < 2^eb
+    if (cmax > 0.f) frexpf(cmax, &ec);
+    if (!isfinite(bound)) eb = 150;
+    if (!isfinite(cmax)) ec = 150;
+    auto clampx = [](int e) { return e > 120 ? 120 : (e < -120 ? -120 : e); };
+    const int sf = clampx(22 - ec), st = clampx(min(29 - eb, 22 - ec));
+    scale = ldexpf(1.0f, st);
+    fine = ldexpf(1.0f, sf);
+    shift = cells ? min(30, sf - st) : 0;
+}
+
 template <int T0, int T1, int T2, int NT>
 __device__ __forceinline__ void deposit_cells_path(const Record<float> *__restrict__ rec,
                                                    const uint32_t *__restrict__ offsets, int ng, int t0, int t1, int t2,
-                                                   int *acc, int fstride, int rw, const float *s_scale)
+                                                   int *acc, int fstride, int rw, const float *s_fine,
+                                                   const int *s_shift)
 {
     constexpr int HL = 2, R0 = T0 + 3, R1 = T1 + 3, RZ = T2 + 3, NW = NT / 32;
-    const float sc[4] = {s_scale[0], s_scale[1], s_scale[2], s_scale[3]};
+    const float fine[4] = {s_fine[0], s_fine[1], s_fine[2], s_fine[3]};
+    const int shift[4] = {s_shift[0], s_shift[1], s_shift[2], s_shift[3]};
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int dz = lane & 3, dy = (lane >> 2) & 3, dxl = lane >> 4;
-    float cxa[4], cxb[4], cyy[4], czz[4];
-    cubic_piece(dxl, cxa);
-    cubic_piece(dxl + 2, cxb);
-    cubic_piece(dy, cyy);
-    cubic_piece(dz, czz);
+    CellPieces pc;
+    cubic_piece(dxl, pc.xa);
+    cubic_piece(dxl + 2, pc.xb);
+    cubic_piece(dy, pc.y);
+    cubic_piece(dz, pc.z);
     auto wrapi = [ng](int a) { return a < 0 ? a + ng : (a >= ng ? a - ng : a); };
     for (int c = warp; c < R0 * R1 * RZ; c += NW) {
         const int r = c / RZ, zz = c % RZ;
@@ -570,29 +638,12 @@ __device__ __forceinline__ void deposit_cells_path(const Record<float> *__restri
         const bool ina = yz && lxa >= 0 && lxa < T0, inb = yz && lxb >= 0 && lxb < T0;
         const int oa = (lxa * T1 + ly) * rw + lz, ob = ((lxa + 2) * T1 + ly) * rw + lz;
         for (uint32_t i0 = beg; i0 < end; i0 += kCellFlush) {
-            const uint32_t i1 = min(end, i0 + kCellFlush);
-            float a[4] = {0.f, 0.f, 0.f, 0.f}, b[4] = {0.f, 0.f, 0.f, 0.f};
-            auto add = [&](const Record<float> &rc) {
-                const float wyz = horner4(cyy, rc.u.y) * horner4(czz, rc.u.z);
-                const float wa = horner4(cxa, rc.u.x) * wyz, wb = horner4(cxb, rc.u.x) * wyz;
-                a[0] += rc.q.x * wa, b[0] += rc.q.x * wb;
-                a[1] += rc.q.y * wa, b[1] += rc.q.y * wb;
-                a[2] += rc.q.z * wa, b[2] += rc.q.z * wb;
-                a[3] += rc.q.w * wa, b[3] += rc.q.w * wb;
-            };
-            uint32_t i = i0;
-            for (; i + 4 <= i1; i += 4) {  // four loads in flight
-                const Record<float> r0 = rec[i], r1 = rec[i + 1], r2 = rec[i + 2], r3 = rec[i + 3];
-                add(r0);
-                add(r1);
-                add(r2);
-                add(r3);
-            }
-            for (; i < i1; ++i) add(rec[i]);
+            int a[4], b[4];
+            cell_chunk(rec, i0, min(end, i0 + kCellFlush), pc, fine, shift, a, b);
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
-                if (ina) atomicAdd(acc + f * fstride + oa, __float2int_rn(a[f] * sc[f]));
-                if (inb) atomicAdd(acc + f * fstride + ob, __float2int_rn(b[f] * sc[f]));
+                if (ina) atomicAdd(acc + f * fstride + oa, a[f]);
+                if (inb) atomicAdd(acc + f * fstride + ob, b[f]);
             }
         }
     }
@@ -631,7 +682,8 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
     __shared__ uint32_t s_beg[C::MAXR];
     __shared__ uint32_t s_pre[C::MAXR + 1];
     __shared__ unsigned s_rowmax;
-    __shared__ float s_scale[4];
+    __shared__ float s_scale[4], s_fine[4];
+    __shared__ int s_shift[4];
 
     const int ntz = ng / T2, nty = ng / T1;
     int tile = blockIdx.x;
@@ -683,16 +735,7 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
         const float m = __uint_as_float(qmax_bits[f]);  // max |q_f| over the catalogue
         const float w3 = kMaxWeight3<M> * 1.0001f;
         const float reach = fminf(static_cast<float>(M * M) * static_cast<float>(s_rowmax), static_cast<float>(total));
-        const float bound = w3 * reach * m;
-        const float cmax = w3 * m;  // largest single contribution
-        int eb = 0, ec = 0;
-        if (bound > 0.f) frexpf(bound, &eb);  // bound < 2^eb
-        if (cmax > 0.f) frexpf(cmax, &ec);
-        if (!isfinite(bound)) eb = 150;
-        if (!isfinite(cmax)) ec = 150;
-        int sexp = dense ? 29 - eb : min(29 - eb, 22 - ec);  // cell sums round with cvt, not FFMA
-        sexp = sexp > 120 ? 120 : (sexp < -120 ? -120 : sexp);
-        s_scale[f] = ldexpf(1.0f, sexp);
+        tile_scales(w3 * reach * m, w3 * m, dense, s_scale[f], s_fine[f], s_shift[f]);
     }
     __syncthreads();
     const float sc0 = s_scale[0], sc1 = s_scale[1], sc2 = s_scale[2], sc3 = s_scale[3];
@@ -702,7 +745,7 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
     bool cells_done = false;
     if constexpr (M == 4) {
         if (dense) {
-            deposit_cells_path<T0, T1, T2, NT>(rec, offsets, ng, t0, t1, t2, acc, TNP, RW, s_scale);
+            deposit_cells_path<T0, T1, T2, NT>(rec, offsets, ng, t0, t1, t2, acc, TNP, RW, s_fine, s_shift);
             cells_done = true;
         }
     }
@@ -749,6 +792,369 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
     }
 }
 
+// ------------------------------------------------------------------ home-tile deposit
+// FP32 grids, cubic order, catalogues with about half a particle per cell or more.
+//
+// Each CTA owns a tile of 16^3 cells and deposits only the particles of those cells
+// (each particle once), into a shared buffer of the 19^3 nodes their stencils reach
+// (nodes -1 .. 17 of the tile on each axis). The 16^3 nodes the tile owns are written
+// to the grid; the 2763 halo nodes go to a per-tile scratch area, and k_home_fixup adds
+// each neighbour's halo to the owned nodes it overlaps, in a fixed order (so the grids
+// do not depend on scheduling).
+//
+// Lane mapping: a warp takes a block of 2 x 16 cells (two x-adjacent cells, 16 z cells)
+// and each lane deposits the first particle of its cell. The buffer's x pitch is 16
+// modulo 32 banks and its z pitch 1, so for every stencil offset the 32 lanes hit 32
+// different banks: the shared atomics of a block take one wavefront each. Particles
+// beyond the first of a cell go to a per-warp queue and are deposited 32 at a time.
+// Tiles with more than two particles per cell, or 32 in some four consecutive cells of a
+// column, take the cell-block path: one warp per cell, each contribution rounded at the
+// fine scale (largest contribution < 2^22) and summed exactly, in 64-bit shared
+// accumulators (two fields per pass), so that a dense node's error is that of its
+// contributions' roundings alone. Tiles with under a quarter particle per cell take one
+// particle per lane from the tile's list.
+//
+// Fixed point as in k_deposit_fx, with bounds over the home tile's own particles (the
+// only ones the buffer receives): B_f = w3 * min(16 * largest 4-cell column window count,
+// particle count) * max |q_f|.
+constexpr int kHomeT = 16;                                      // tile edge in cells (= owned nodes)
+constexpr int kHomeB = kHomeT + 3;                              // buffer edge in nodes
+constexpr int kHomePY = kHomeB;                                 // buffer y pitch
+constexpr int kHomePX = 368;                                    // buffer x pitch
+constexpr int kHomeField = kHomeB * kHomePX;                    // ints per field
+constexpr int kHomeHalo = kHomeB * kHomeB * kHomeB - kHomeT * kHomeT * kHomeT;  // 2763 halo nodes
+constexpr int kHomeNT = 256;                                    // one thread per cell column of the tile
+constexpr int kHomeNW = kHomeNT / 32;
+constexpr int kHomeQ = 64;                                      // overflow queue entries per warp
+constexpr size_t kHomeSmem = size_t(4) * kHomeField * sizeof(int);
+static_assert(kHomePX % 32 == 16 && kHomePX >= kHomeB * kHomeB, "x-adjacent cells must be 16 banks apart");
+static_assert(kHomeNT == kHomeT * kHomeT, "one thread per cell column");
+static_assert(kHomeNW * kHomeQ <= 2 * kHomeNT + 1, "queues share the column-range arrays");
+
+// Halo index of buffer node (bx, by, bz), at least one coordinate in {0, 17, 18}:
+// first the three x planes (19 x 19 each), then the y planes of the inner x range
+// (16 x 19), then the z planes of the inner x, y range (16 x 16).
+__device__ __forceinline__ int home_side(int b) { return b == 0 ? 0 : b - kHomeT; }  // 0, 17, 18 -> 0, 1, 2
+__device__ __forceinline__ int home_unside(int s) { return s == 0 ? 0 : s + kHomeT; }
+__device__ __forceinline__ int home_halo_index(int bx, int by, int bz)
+{
+    if (bx == 0 || bx > kHomeT) return (home_side(bx) * kHomeB + by) * kHomeB + bz;
+    if (by == 0 || by > kHomeT) return 3 * kHomeB * kHomeB + ((bx - 1) * 3 + home_side(by)) * kHomeB + bz;
+    return 3 * kHomeB * kHomeB + 3 * kHomeT * kHomeB + ((bx - 1) * kHomeT + (by - 1)) * 3 + home_side(bz);
+}
+__device__ __forceinline__ void home_halo_node(int k, int &bx, int &by, int &bz)
+{
+    constexpr int nx = 3 * kHomeB * kHomeB, ny = 3 * kHomeT * kHomeB;
+    if (k < nx) {
+        bz = k % kHomeB;
+        const int r = k / kHomeB;
+        by = r % kHomeB;
+        bx = home_unside(r / kHomeB);
+    } else if (k < nx + ny) {
+        k -= nx;
+        bz = k % kHomeB;
+        const int r = k / kHomeB;
+        by = home_unside(r % 3);
+        bx = r / 3 + 1;
+    } else {
+        k -= nx + ny;
+        bz = home_unside(k % 3);
+        const int r = k / 3;
+        by = r % kHomeT + 1;
+        bx = r / kHomeT + 1;
+    }
+}
+
+// One particle of home cell (cx, cy, cz) (each 0..15) into the node buffer: node
+// c - 1 + k of the tile is buffer index c + k.
+__device__ __forceinline__ void home_particle(int *acc, const Record<float> &r, int cx, int cy, int cz, float sc0,
+                                              float sc1, float sc2, float sc3)
+{
+    constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+    constexpr int kMagicBits = 0x4B400000;
+    float wx[4], wy[4], wz[4];
+    int first;
+    bspline_weights<4, float>(r.u.x, wx, first);
+    bspline_weights<4, float>(r.u.y, wy, first);
+    bspline_weights<4, float>(r.u.z, wz, first);
+    const float q0 = r.q.x * sc0, q1 = r.q.y * sc1, q2 = r.q.z * sc2, q3 = r.q.w * sc3;
+    const int base = cx * kHomePX + cy * kHomePY + cz;
+#pragma unroll
+    for (int k0 = 0; k0 < 4; ++k0) {
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            const float w01 = wx[k0] * wy[k1];
+            int *b = acc + base + k0 * kHomePX + k1 * kHomePY;
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) {
+                const float ww = w01 * wz[k2];
+                int *a = b + k2;
+                atomicAdd(a, __float_as_int(fmaf(q0, ww, kMagic)) - kMagicBits);
+                atomicAdd(a + kHomeField, __float_as_int(fmaf(q1, ww, kMagic)) - kMagicBits);
+                atomicAdd(a + 2 * kHomeField, __float_as_int(fmaf(q2, ww, kMagic)) - kMagicBits);
+                atomicAdd(a + 3 * kHomeField, __float_as_int(fmaf(q3, ww, kMagic)) - kMagicBits);
+            }
+        }
+    }
+}
+
+// A sorted particle of this tile (its cell read from the record); skipped if the record
+// does not lie in the tile.
+__device__ __forceinline__ void home_listed(int *acc, const Record<float> &r, int t0, int t1, int t2, float sc0,
+                                            float sc1, float sc2, float sc3)
+{
+    const int c = unpack_cell(r.u.w);
+    const unsigned cx = static_cast<unsigned>((c & 1023) - t0), cy = static_cast<unsigned>(((c >> 10) & 1023) - t1),
+                   cz = static_cast<unsigned>(((c >> 20) & 1023) - t2);
+    if (cx < kHomeT && cy < kHomeT && cz < kHomeT)
+        home_particle(acc, r, static_cast<int>(cx), static_cast<int>(cy), static_cast<int>(cz), sc0, sc1, sc2, sc3);
+}
+
+// Dense home tiles: one warp per occupied cell; lane l owns stencil nodes (dx, dy, dz)
+// with dz = l & 3, dy = (l >> 2) & 3, dx = (l >> 4) and (l >> 4) + 2, sums up to
+// kCellFlush of the cell's particles in FP32 registers and adds the rounded sums.
+template <int F0>
+__device__ __forceinline__ void home_cells_path(const Record<float> *__restrict__ rec,
+                                                const uint32_t *__restrict__ offsets, int ng, int t0, int t1, int t2,
+                                                unsigned long long *acc, const float *s_fine)
+{
+    const float fine[4] = {s_fine[0], s_fine[1], s_fine[2], s_fine[3]};
+    const int noshift[4] = {0, 0, 0, 0};
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int dz = lane & 3, dy = (lane >> 2) & 3, dxl = lane >> 4;
+    CellPieces pc;
+    cubic_piece(dxl, pc.xa);
+    cubic_piece(dxl + 2, pc.xb);
+    cubic_piece(dy, pc.y);
+    cubic_piece(dz, pc.z);
+    for (int c = warp; c < kHomeT * kHomeT * kHomeT; c += kHomeNW) {
+        const int cx = c >> 8, cy = (c >> 4) & 15, cz = c & 15;
+        const int64_t key = (static_cast<int64_t>(t0 + cx) * ng + (t1 + cy)) * ng + (t2 + cz);
+        const uint32_t beg = offsets[key], end = offsets[key + 1];
+        if (beg == end) continue;
+        const int oa = (cx + dxl) * kHomePX + (cy + dy) * kHomePY + cz + dz, ob = oa + 2 * kHomePX;
+        for (uint32_t i0 = beg; i0 < end; i0 += kCellFlush) {
+            int a[2], b[2];
+            cell_chunk<F0, 2>(rec, i0, min(end, i0 + kCellFlush), pc, fine, noshift, a, b);
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {  // two's complement sums
+                atomicAdd(acc + f * kHomeField + oa, static_cast<unsigned long long>(static_cast<long long>(a[f])));
+                atomicAdd(acc + f * kHomeField + ob, static_cast<unsigned long long>(static_cast<long long>(b[f])));
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kHomeNT, 2)
+k_deposit_home(const Record<float> *__restrict__ rec, const uint32_t *__restrict__ offsets,
+               const unsigned *__restrict__ qmax_bits, int ng, float *__restrict__ grids, int64_t grid_elems,
+               float *__restrict__ halo)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int *acc = reinterpret_cast<int *>(smem_raw);  // [4][kHomeB][kHomePX] (x, y, z of the node buffer)
+    // column ranges of the tile (sparse path), reused as the per-warp queues (medium path)
+    __shared__ uint32_t s_cols[2 * kHomeNT + 1];
+    uint32_t *s_beg = s_cols, *s_pre = s_cols + kHomeNT;
+    __shared__ unsigned s_rowmax;
+    __shared__ float s_scale[4], s_fine[4];
+    __shared__ int s_shift[4];
+
+    const int nt = ng / kHomeT;
+    const int tz = blockIdx.x % nt, ty = (blockIdx.x / nt) % nt, tx = blockIdx.x / (nt * nt);
+    const int t0 = tx * kHomeT, t1 = ty * kHomeT, t2 = tz * kHomeT;
+    {
+        int4 *a4 = reinterpret_cast<int4 *>(acc);
+        for (int k = threadIdx.x; k < kHomeField; k += kHomeNT) a4[k] = make_int4(0, 0, 0, 0);  // 4 fields / 4 ints
+    }
+    if (threadIdx.x == 0) s_rowmax = 0;
+    __syncthreads();
+    // thread = cell column (x, y) of the tile: its particles are one range of the sort
+    uint32_t total;
+    {
+        const int x = threadIdx.x >> 4, y = threadIdx.x & 15;
+        const int64_t key = (static_cast<int64_t>(t0 + x) * ng + (t1 + y)) * ng + t2;
+        uint32_t o[kHomeT + 1];
+#pragma unroll
+        for (int z = 0; z <= kHomeT; ++z) o[z] = offsets[key + z];
+        const uint32_t b = o[0], cnt = o[kHomeT] - b;
+        // a node receives from 4 consecutive cells of a column: the largest such count
+        uint32_t win = 0;
+#pragma unroll
+        for (int z = 0; z + 4 <= kHomeT; ++z) win = max(win, o[z + 4] - o[z]);
+        const uint32_t pre = block_exclusive_scan(cnt, total);
+        s_beg[threadIdx.x] = b;
+        s_pre[threadIdx.x] = pre;
+        if (threadIdx.x == 0) s_pre[kHomeNT] = total;
+        if (win) atomicMax(&s_rowmax, win);
+    }
+    __syncthreads();
+    constexpr uint32_t kCells = kHomeT * kHomeT * kHomeT;
+    // dense somewhere (32 particles in four consecutive cells) or on average: sum each
+    // cell in registers and round once per cell, instead of once per particle
+    const bool dense = s_rowmax >= 32u || total > 2u * kCells;
+    const bool sparse = !dense && total < kCells / 4u;
+    if (threadIdx.x < 4) {
+        const int f = threadIdx.x;
+        const float m = __uint_as_float(qmax_bits[f]);  // max |q_f| over the catalogue
+        const float w3 = kMaxWeight3<4> * 1.0001f;
+        // a node receives from 4 consecutive cells of at most 4 x 4 columns of the tile
+        const float reach = fminf(16.0f * static_cast<float>(s_rowmax), static_cast<float>(total));
+        tile_scales(w3 * reach * m, w3 * m, dense, s_scale[f], s_fine[f], s_shift[f]);
+    }
+    __syncthreads();
+    const float sc0 = s_scale[0], sc1 = s_scale[1], sc2 = s_scale[2], sc3 = s_scale[3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    // owned nodes to the grid, halo nodes to this tile's scratch; value(f, buffer index)
+    float *h = halo + static_cast<int64_t>(blockIdx.x) * 4 * kHomeHalo;
+    auto emit = [&](int f, auto value) {
+        for (int k = threadIdx.x; k < static_cast<int>(kCells); k += kHomeNT) {
+            const int z = k & 15, y = (k >> 4) & 15, x = k >> 8;
+            const int64_t gi = (static_cast<int64_t>(t0 + x) * ng + (t1 + y)) * (ng + 2) + t2 + z;
+            grids[f * grid_elems + gi] = value((x + 1) * kHomePX + (y + 1) * kHomePY + z + 1);
+        }
+        for (int k = threadIdx.x; k < kHomeHalo; k += kHomeNT) {
+            int bx, by, bz;
+            home_halo_node(k, bx, by, bz);
+            h[f * kHomeHalo + k] = value(bx * kHomePX + by * kHomePY + bz);
+        }
+    };
+
+    if (dense) {
+        // 64-bit sums of the fine-scale contributions, two fields per pass in the same buffer
+        auto *acc64 = reinterpret_cast<unsigned long long *>(smem_raw);  // [2][kHomeB][kHomePX]
+#pragma unroll
+        for (int pass = 0; pass < 2; ++pass) {
+            if (pass) {
+                __syncthreads();
+                int4 *a4 = reinterpret_cast<int4 *>(smem_raw);
+                for (int k = threadIdx.x; k < kHomeField; k += kHomeNT) a4[k] = make_int4(0, 0, 0, 0);
+                __syncthreads();
+            }
+            if (pass == 0) home_cells_path<0>(rec, offsets, ng, t0, t1, t2, acc64, s_fine);
+            else home_cells_path<2>(rec, offsets, ng, t0, t1, t2, acc64, s_fine);
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int f = 2 * pass + k;
+                const float inv = 1.0f / s_fine[f];  // exact: a power of two
+                const unsigned long long *a = acc64 + k * kHomeField;
+                emit(f, [&](int ai) { return static_cast<float>(static_cast<long long>(a[ai])) * inv; });
+            }
+        }
+        return;
+    }
+    if (sparse) {
+        // one particle per lane, warp-contiguous chunks of the tile's list
+        const uint32_t per_warp = ((total + kHomeNW - 1) / kHomeNW + 31u) & ~31u;
+        const uint32_t wbeg = static_cast<uint32_t>(warp) * per_warp, wend = min(wbeg + per_warp, total);
+        int slot = wbeg + lane < wend ? find_slot<kHomeNT>(s_pre, wbeg + lane) : 0;
+        for (uint32_t p = wbeg + lane; p < wend; p += 32) {
+            while (p >= s_pre[slot + 1]) ++slot;
+            home_listed(acc, rec[s_beg[slot] + (p - s_pre[slot])], t0, t1, t2, sc0, sc1, sc2, sc3);
+        }
+    } else {
+        uint32_t *q = s_cols + warp * kHomeQ;  // the column ranges are no longer needed
+        __syncthreads();
+        int qn = 0;  // warp-uniform queue length
+        const int xl = lane >> 4, cz = lane & 15;
+        for (int blk = warp; blk < kHomeT * kHomeT / 2; blk += kHomeNW) {
+            const int cy = blk & 15, cx = 2 * (blk >> 4) + xl;
+            const int64_t key = (static_cast<int64_t>(t0 + cx) * ng + (t1 + cy)) * ng + (t2 + cz);
+            const uint32_t beg = offsets[key], end = offsets[key + 1];
+            if (end > beg) home_particle(acc, rec[beg], cx, cy, cz, sc0, sc1, sc2, sc3);
+            uint32_t next = beg + 1, extra = end > beg ? end - beg - 1 : 0u;
+            while (__any_sync(0xffffffffu, extra > 0u)) {
+                const bool has = extra > 0u;
+                const unsigned m = __ballot_sync(0xffffffffu, has);
+                if (has) {
+                    q[qn + __popc(m & ((1u << lane) - 1u))] = next;
+                    ++next;
+                    --extra;
+                }
+                qn += __popc(m);
+                __syncwarp();
+                if (qn >= 32) {
+                    home_listed(acc, rec[q[lane]], t0, t1, t2, sc0, sc1, sc2, sc3);
+                    __syncwarp();
+                    if (lane < qn - 32) q[lane] = q[lane + 32];
+                    qn -= 32;
+                    __syncwarp();
+                }
+            }
+        }
+        if (lane < qn) home_listed(acc, rec[q[lane]], t0, t1, t2, sc0, sc1, sc2, sc3);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const float inv = 1.0f / s_scale[f];  // exact: a power of two
+        const int *a = acc + f * kHomeField;
+        emit(f, [&](int ai) { return static_cast<float>(a[ai]) * inv; });
+    }
+}
+
+// Owned nodes within reach of a neighbouring tile's particles (local index 0, 1 or 15
+// on some axis) receive that neighbour's halo values, added in a fixed order.
+__global__ void __launch_bounds__(256)
+k_home_fixup(const float *__restrict__ halo, int ng, float *__restrict__ grids, int64_t grid_elems)
+{
+    const int nt = ng / kHomeT;
+    const int tz = blockIdx.x % nt, ty = (blockIdx.x / nt) % nt, tx = blockIdx.x / (nt * nt);
+    auto wrap = [nt](int a) { return a < 0 ? a + nt : (a >= nt ? a - nt : a); };
+    auto edge = [](int l) { return l <= 1 || l == kHomeT - 1; };
+    // offsets d on one axis whose tile's halo covers local index l: 0, -1 (l = 0, 1), +1 (l = 15)
+    auto dlo = [](int l) { return l <= 1 ? -1 : 0; };
+    auto dhi = [](int l) { return l == kHomeT - 1 ? 1 : 0; };
+    for (int k = threadIdx.x; k < kHomeT * kHomeT * kHomeT; k += blockDim.x) {
+        const int z = k & 15, y = (k >> 4) & 15, x = k >> 8;
+        if (!(edge(x) || edge(y) || edge(z))) continue;
+        const int64_t gi = (static_cast<int64_t>(tx * kHomeT + x) * ng + (ty * kHomeT + y)) * (ng + 2) + tz * kHomeT + z;
+        float v[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) v[f] = grids[f * grid_elems + gi];
+        for (int dx = dlo(x); dx <= dhi(x); ++dx)
+            for (int dy = dlo(y); dy <= dhi(y); ++dy)
+                for (int dz = dlo(z); dz <= dhi(z); ++dz) {
+                    if (dx == 0 && dy == 0 && dz == 0) continue;
+                    const int nb = (wrap(tx + dx) * nt + wrap(ty + dy)) * nt + wrap(tz + dz);
+                    const int hi = home_halo_index(x - kHomeT * dx + 1, y - kHomeT * dy + 1, z - kHomeT * dz + 1);
+                    const float *hp = halo + static_cast<int64_t>(nb) * 4 * kHomeHalo + hi;
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) v[f] += hp[f * kHomeHalo];
+                }
+#pragma unroll
+        for (int f = 0; f < 4; ++f) grids[f * grid_elems + gi] = v[f];
+    }
+}
+
+cudaError_t launch_home(const AssignPlan &pl, const uint32_t *offsets, const unsigned *qmax, const Record<float> *rec,
+                        void *grids, float *halo, cudaStream_t s)
+{
+    constexpr int kMaxDev = 64;
+    static bool configured[kMaxDev] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDev || !configured[dev]) {
+        e = cudaFuncSetAttribute(k_deposit_home, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kHomeSmem));
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_deposit_home, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < kMaxDev) configured[dev] = true;
+    }
+    const int ng = pl.ng;
+    const unsigned tiles = static_cast<unsigned>((ng / kHomeT) * (ng / kHomeT) * (ng / kHomeT));
+    const int64_t grid_elems = static_cast<int64_t>(ng) * ng * (ng + 2);
+    auto *g = static_cast<float *>(grids);
+    k_deposit_home<<<tiles, kHomeNT, kHomeSmem, s>>>(rec, offsets, qmax, ng, g, grid_elems, halo);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_home_fixup<<<tiles, 256, 0, s>>>(halo, ng, g, grid_elems);
+    return cudaGetLastError();
+}
+
 struct TileDesc {
     int prec;
     int d[3];
@@ -761,6 +1167,7 @@ constexpr TileDesc kTiles[] = {
     {PKMOM_F64, {8, 8, 16}},    // 4
     {PKMOM_F64, {16, 16, 16}},  // 5
     {PKMOM_F64, {8, 8, 8}},     // 6
+    {PKMOM_F32, {16, 16, 16}},  // 7: home tiles (cubic order; other orders use tile 0)
 };
 
 template <typename T, int M, int T0, int T1, int T2, int NT>
@@ -799,7 +1206,7 @@ cudaError_t launch_deposit_t(const AssignPlan &pl, const uint32_t *offsets, cons
 
 template <int M>
 cudaError_t launch_deposit_m(const AssignPlan &pl, const uint32_t *offsets, const unsigned *q, const void *rec,
-                             void *grids, cudaStream_t s)
+                             void *grids, float *halo, cudaStream_t s)
 {
     const auto *rf = static_cast<const Record<float> *>(rec);
     const auto *rd = static_cast<const Record<double> *>(rec);
@@ -811,6 +1218,9 @@ cudaError_t launch_deposit_m(const AssignPlan &pl, const uint32_t *offsets, cons
     case 4: return launch_deposit_t<double, M, 8, 8, 16, 256>(pl, offsets, q, rd, grids, s);
     case 5: return launch_deposit_t<double, M, 16, 16, 16, 256>(pl, offsets, q, rd, grids, s);
     case 6: return launch_deposit_t<double, M, 8, 8, 8, 128>(pl, offsets, q, rd, grids, s);
+    case 7:
+        if constexpr (M == 4) return launch_home(pl, offsets, q, rf, grids, halo, s);
+        else return launch_deposit_t<float, M, 16, 16, 16, 256>(pl, offsets, q, rf, grids, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -821,6 +1231,12 @@ const T *tp(const void *p) { return static_cast<const T *>(p); }
 }  // namespace
 
 int deposit_tile_count() { return static_cast<int>(sizeof(kTiles) / sizeof(kTiles[0])); }
+
+size_t home_halo_bytes(int ng)
+{
+    const size_t tiles = size_t(ng / kHomeT) * (ng / kHomeT) * (ng / kHomeT);
+    return tiles * 4 * kHomeHalo * sizeof(float);
+}
 
 void deposit_tile_shape(int tile, int prec, int dims[3])
 {
@@ -911,15 +1327,16 @@ cudaError_t launch_deposit(const AssignPlan &pl, void *scratch, void *grids, cud
     auto *offsets = reinterpret_cast<const uint32_t *>(sc + pl.off_counts);
     auto *qmax = reinterpret_cast<const unsigned *>(sc + pl.off_qmax);
     const void *rec = sc + pl.off_records;
+    float *halo = pl.off_halo ? reinterpret_cast<float *>(sc + pl.off_halo) : nullptr;
     cudaError_t e;
     switch (pl.order) {
-    case 1: e = launch_deposit_m<1>(pl, offsets, qmax, rec, grids, s); break;
-    case 2: e = launch_deposit_m<2>(pl, offsets, qmax, rec, grids, s); break;
-    case 3: e = launch_deposit_m<3>(pl, offsets, qmax, rec, grids, s); break;
-    case 4: e = launch_deposit_m<4>(pl, offsets, qmax, rec, grids, s); break;
+    case 1: e = launch_deposit_m<1>(pl, offsets, qmax, rec, grids, halo, s); break;
+    case 2: e = launch_deposit_m<2>(pl, offsets, qmax, rec, grids, halo, s); break;
+    case 3: e = launch_deposit_m<3>(pl, offsets, qmax, rec, grids, halo, s); break;
+    case 4: e = launch_deposit_m<4>(pl, offsets, qmax, rec, grids, halo, s); break;
     default: return cudaErrorInvalidValue;
     }
-    st.launches++;
+    st.launches += (pl.tile == kHomeTile && pl.order == 4) ? 2 : 1;
     return e;
 }
 

@@ -129,6 +129,10 @@ AssignPlan plan_assign(const pkmom_params &p, int64_t n, int num_sms, int tile_o
             break;
         }
     }
+    // cubic order at half a particle per cell or more: home tiles (each particle deposited
+    // once, by the tile owning its cell)
+    const double ppc = double(n) / cells;
+    if (p.precision == PKMOM_F32 && p.order == 4 && p.ng % 16 == 0 && ppc >= 0.5) pl.tile = kHomeTile;
     if (tile_override >= 0) {
         int d[3];
         deposit_tile_shape(tile_override, p.precision, d);
@@ -143,9 +147,9 @@ AssignPlan plan_assign(const pkmom_params &p, int64_t n, int num_sms, int tile_o
     while ((1 << (sshift + 1)) <= td[2] && (p.ng % (1 << (sshift + 1))) == 0 && cells / (1 << sshift) > double(1u << 30))
         ++sshift;
     pl.sshift = sshift;
+    if (pl.tile == kHomeTile && sshift != 0) pl.tile = 0;  // home tiles need one sort key per cell
     // sparse catalogues: list each tile's particles in shared memory (room for about
     // twice the expected count of its reach; larger tiles fall back to searching)
-    const double ppc = double(n) / cells;
     const double reach = double(td[0] + 3) * (td[1] + 3) * (td[2] + 3);
     if (p.precision == PKMOM_F32 && ppc < 0.5) {
         const double want = 2.0 * ppc * reach + 64.0;
@@ -169,6 +173,10 @@ AssignPlan plan_assign(const pkmom_params &p, int64_t n, int num_sms, int tile_o
     off = align_up(off + size_t(pl.scan_blocks + 1) * 4);
     pl.off_qmax = off;
     off = align_up(off + 4 * sizeof(unsigned));
+    if (pl.tile == kHomeTile && p.order == 4) {
+        pl.off_halo = off;
+        off = align_up(off + home_halo_bytes(p.ng));
+    }
     pl.total = off;
     return pl;
 }

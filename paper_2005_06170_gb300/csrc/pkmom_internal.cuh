@@ -35,6 +35,7 @@ struct AssignPlan {
     int hist_blocks = 0;     // blocks of the moments+histogram kernel
     int64_t scan_blocks = 0; // blocks of the key scan
     size_t off_counts = 0, off_ranks = 0, off_records = 0, off_partials = 0, off_blocksums = 0, off_qmax = 0;
+    size_t off_halo = 0;     // home-tile deposit: per-tile halo nodes (0 = not used)
     size_t total = 0;
 };
 
@@ -52,6 +53,10 @@ cudaError_t launch_scatter(const pkmom_catalog &cat, const AssignPlan &pl, doubl
                            cudaStream_t s, LaunchStats &st);
 cudaError_t launch_deposit(const AssignPlan &pl, void *scratch, void *grids, cudaStream_t s, LaunchStats &st);
 // Tile shapes the deposit kernel is instantiated for (x, y, z nodes).
+// Tile kHomeTile (16^3, FP32) deposits each particle once in the tile owning its cell
+// (cubic order; it needs home_halo_bytes of scratch); other orders use the 16^3 gather.
+constexpr int kHomeTile = 7;
+size_t home_halo_bytes(int ng);
 int deposit_tile_count();
 void deposit_tile_shape(int tile, int prec, int dims[3]);
 

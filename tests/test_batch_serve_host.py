@@ -65,6 +65,7 @@ def test_autotune_candidates_and_classes():
     assert autotune.density_class(1, 1024) == -10
     c = autotune.candidates(256, 0)
     assert (0, -1) in c and (1, 0) in c and (3, -1) in c
+    assert (7, -1) in c and (7, 0) not in c  # home tiles keep no particle list
     assert all(t in autotune.F32_TILES for t, _ in c)
     c40 = autotune.candidates(40, 0)
     assert {t for t, _ in c40} == {3}  # only 8x8x8 divides 40

@@ -140,6 +140,50 @@ def test_assigned_grids_match_oracle(ctx, gpu_lib, order, dtype, ng):
         assert np.max(np.abs(g[f] - ref[f])) <= tol, (f, np.max(np.abs(g[f] - ref[f])) / scale)
 
 
+def _clustered(n, L, seed):
+    """Half the particles in a Gaussian blob (sigma = L/16) at the centre, 40 % uniform in
+    the slab x < L/3, 10 % uniform in the box: 16^3-cell tiles of every density class."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nb, ns = n // 2, (2 * n) // 5
+    nu = n - nb - ns
+    blob = rng.normal(L / 2, L / 16, (nb, 3))
+    slab = rng.uniform(0, L, (ns, 3))
+    slab[:, 0] /= 3
+    pos = np.mod(np.concatenate([blob, slab, rng.uniform(0, L, (nu, 3))]), L).astype(np.float32)
+    pos[pos >= np.float32(L)] = 0
+    vel = rng.normal(0, 300, (n, 3)).astype(np.float32)
+    return {"pos": pos, "vel": vel}
+
+
+@pytest.mark.parametrize("kind,ng,n,tile", [("uniform", 32, 40000, -1), ("clustered", 48, 66355, -1),
+                                            ("uniform", 64, 20000, 7), ("clustered", 32, 20000, 7)])
+def test_home_tile_grids_match_oracle(ctx, gpu_lib, kind, ng, n, tile):
+    """Home-tile deposit (each particle once by the tile owning its cell, halos added by a
+    fix-up pass): uniform catalogues (one particle per lane of a 2 x 16 cell block, extra
+    particles queued), clustered ones (dense, medium and sparse tiles in one launch), and
+    the tile forced below half a particle per cell."""
+    import torch
+    pk = gpu_lib
+    L = 200.0
+    cat = catalogs.poisson(n, L, seed=90 + ng, dtype=np.float32) if kind == "uniform" else _clustered(n, L, 91 + ng)
+    p = pk.params(L, ng, 8)
+    pos, vel, mass = to_dev(cat, torch)
+    grids = torch.empty((4, ng, ng, ng + 2), dtype=torch.float32, device="cuda")
+    mom = torch.zeros(16, dtype=torch.float64, device="cuda")
+    ctx.set_tuning(tile, -1)
+    try:
+        scratch = torch.empty(ctx.scratch_bytes_tuned(p, n), dtype=torch.uint8, device="cuda")
+        ctx.assign(pk.catalog_from_tensors(pos, vel, mass), p, grids, mom, scratch)
+        ctx.sync()
+    finally:
+        ctx.set_tuning(-1, -1)
+    g = grids[..., :ng].double().cpu().numpy()
+    ref = est.assign(cat["pos"], cat["vel"], None, L=L, ng=ng, order=4)
+    for f in range(4):
+        scale = np.abs(ref[f]).max()
+        assert np.max(np.abs(g[f] - ref[f])) <= 1e-5 * scale, (f, np.max(np.abs(g[f] - ref[f])) / scale)
+
+
 # ------------------------------------------------------------------ whole estimator
 
 def test_config1_fp64_poisson(ctx, gpu_lib):
