@@ -4,12 +4,12 @@
 //
 // Pipeline (all on one stream):
 //   k_hist_moments  one pass over the catalogue: FP64 moments (block partials) and a
-//                   histogram of sort keys (key = x-row, y-row, z-segment of the cell);
-//                   each particle keeps the rank its atomic increment returned.
+//                   histogram of sort keys (key = x-row, y-row, z-segment of the cell).
 //   k_moments_final fixed-order sum of the block partials -> pkmom_moments.
 //   k_scan_*        exclusive scan of the key counts -> segment offsets.
 //   k_scatter       writes each particle as a 32-byte record (grid coordinates and the
-//                   four deposited values) at offset[key] + rank: a counting sort.
+//                   four deposited values) at the slot an atomic increment of its key's
+//                   cursor returns: a counting sort (any order within a key).
 //   k_deposit       one CTA per output tile of grid nodes: gathers the particles of
 //                   every segment whose stencils reach the tile (tile + halo, located
 //                   through the offsets), accumulates B-spline weights x values in
@@ -33,8 +33,12 @@ template <typename T>
 __device__ __forceinline__ bool cell_of(T u, int ng, int &c)
 {
     if (!(fabs(u) < T(1 << 30))) return false;
-    int ic = static_cast<int>(floor(u)) % ng;
-    c = ic < 0 ? ic + ng : ic;
+    int ic = static_cast<int>(floor(u));
+    if (static_cast<unsigned>(ic) >= static_cast<unsigned>(ng)) {  // outside the box: wrap
+        ic %= ng;
+        ic = ic < 0 ? ic + ng : ic;
+    }
+    c = ic;
     return true;
 }
 
@@ -54,8 +58,7 @@ template <> __device__ __forceinline__ double pack_cell<double>(int c0, int c1, 
 __device__ __forceinline__ int unpack_cell(float v) { return __float_as_int(v); }
 __device__ __forceinline__ int unpack_cell(double v) { return static_cast<int>(v); }
 
-// One pass over the catalogue: the histogram of sort keys (each particle keeps the
-// rank its atomic increment returned) and the moments. Each lane sums kGroup
+// One pass over the catalogue: the histogram of sort keys and the moments. Each lane sums kGroup
 // particles in the catalogue precision; the warp then adds its lanes' group sums
 // (shuffles) and lane 0 adds the result to FP64 accumulators, so that FP64 work is
 // one add per value per 32 * kGroup particles. Two particles per iteration keep more
@@ -65,7 +68,7 @@ __global__ void __launch_bounds__(kHistThreads, 4)
 k_hist_moments(const T *__restrict__ x, const T *__restrict__ y, const T *__restrict__ z,
                const T *__restrict__ vx, const T *__restrict__ vy, const T *__restrict__ vz,
                const T *__restrict__ mass, int64_t stride, int64_t n, T scale, int ng, int sshift,
-               uint32_t *__restrict__ counts, uint32_t *__restrict__ ranks, double *__restrict__ partials,
+               uint32_t *__restrict__ counts, double *__restrict__ partials,
                unsigned *__restrict__ qmax_bits, int *__restrict__ err)
 {
     const int nseg = ng >> sshift;
@@ -98,14 +101,12 @@ k_hist_moments(const T *__restrict__ x, const T *__restrict__ y, const T *__rest
         const T v0 = vx[j], v1 = vy[j], v2 = vz[j];
         int c0, c1, c2;
         const bool ok = cell_of(u0, ng, c0) & cell_of(u1, ng, c1) & cell_of(u2, ng, c2);
-        uint32_t rank = 0xffffffffu;
         if (ok) {
             const int64_t key = (static_cast<int64_t>(c0) * ng + c1) * nseg + (c2 >> sshift);
-            rank = atomicAdd(counts + key, 1u);
+            atomicAdd(counts + key, 1u);  // no value returned: the scatter takes the slots
         } else {
             *err = 1;
         }
-        ranks[i] = rank;
         const T m2 = m * m;
         qmax[0] = fmaxf(qmax[0], static_cast<float>(fabs(m)));
         qmax[1] = fmaxf(qmax[1], static_cast<float>(fabs(m * v0)));
@@ -290,22 +291,17 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 k_scatter(const T *__restrict__ x, const T *__restrict__ y, const T *__restrict__ z, const T *__restrict__ vx,
           const T *__restrict__ vy, const T *__restrict__ vz, const T *__restrict__ mass, int64_t stride, int64_t n,
-          T scale, int ng, int sshift, const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ ranks,
-          Record<T> *__restrict__ rec)
+          T scale, int ng, int sshift, uint32_t *__restrict__ cursor, Record<T> *__restrict__ rec)
 {
     const int nseg = ng >> sshift;
     const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += step) {
-        const uint32_t rank = ranks[i];
-        if (rank == 0xffffffffu) continue;
         const int64_t j = i * stride;
         const T u0 = mul_rn(x[j], scale), u1 = mul_rn(y[j], scale), u2 = mul_rn(z[j], scale);
         int c0, c1, c2;
-        cell_of(u0, ng, c0);
-        cell_of(u1, ng, c1);
-        cell_of(u2, ng, c2);
+        if (!(cell_of(u0, ng, c0) & cell_of(u1, ng, c1) & cell_of(u2, ng, c2))) continue;  // reported by the histogram
         const int64_t key = (static_cast<int64_t>(c0) * ng + c1) * nseg + (c2 >> sshift);
-        const uint32_t dst = offsets[key] + rank;
+        const uint32_t dst = atomicAdd(cursor + key, 1u);
         const T m = mass ? mass[i] : T(1);
         Record<T> r;
         r.u = Vec4<T>{u0 - floor(u0), u1 - floor(u1), u2 - floor(u2), pack_cell<T>(c0, c1, c2)};
@@ -865,6 +861,13 @@ __device__ __forceinline__ void home_halo_node(int k, int &bx, int &by, int &bz)
     }
 }
 
+// Shared-memory add without a returned value (the accumulators are read only after a
+// barrier): addr is a shared-window byte address.
+__device__ __forceinline__ void red_shared_add(unsigned addr, int v)
+{
+    asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+
 // One particle of home cell (cx, cy, cz) (each 0..15) into the node buffer: node
 // c - 1 + k of the tile is buffer index c + k.
 __device__ __forceinline__ void home_particle(int *acc, const Record<float> &r, int cx, int cy, int cz, float sc0,
@@ -878,21 +881,22 @@ __device__ __forceinline__ void home_particle(int *acc, const Record<float> &r, 
     bspline_weights<4, float>(r.u.y, wy, first);
     bspline_weights<4, float>(r.u.z, wz, first);
     const float q0 = r.q.x * sc0, q1 = r.q.y * sc1, q2 = r.q.z * sc2, q3 = r.q.w * sc3;
-    const int base = cx * kHomePX + cy * kHomePY + cz;
+    // shared-window byte address of the particle's first stencil node
+    const unsigned base = static_cast<unsigned>(__cvta_generic_to_shared(acc)) + 4u * (cx * kHomePX + cy * kHomePY + cz);
 #pragma unroll
     for (int k0 = 0; k0 < 4; ++k0) {
 #pragma unroll
         for (int k1 = 0; k1 < 4; ++k1) {
             const float w01 = wx[k0] * wy[k1];
-            int *b = acc + base + k0 * kHomePX + k1 * kHomePY;
+            const unsigned b = base + 4u * (k0 * kHomePX + k1 * kHomePY);
 #pragma unroll
             for (int k2 = 0; k2 < 4; ++k2) {
                 const float ww = w01 * wz[k2];
-                int *a = b + k2;
-                atomicAdd(a, __float_as_int(fmaf(q0, ww, kMagic)) - kMagicBits);
-                atomicAdd(a + kHomeField, __float_as_int(fmaf(q1, ww, kMagic)) - kMagicBits);
-                atomicAdd(a + 2 * kHomeField, __float_as_int(fmaf(q2, ww, kMagic)) - kMagicBits);
-                atomicAdd(a + 3 * kHomeField, __float_as_int(fmaf(q3, ww, kMagic)) - kMagicBits);
+                const unsigned a = b + 4 * k2;
+                red_shared_add(a, __float_as_int(fmaf(q0, ww, kMagic)) - kMagicBits);
+                red_shared_add(a + 4 * kHomeField, __float_as_int(fmaf(q1, ww, kMagic)) - kMagicBits);
+                red_shared_add(a + 8 * kHomeField, __float_as_int(fmaf(q2, ww, kMagic)) - kMagicBits);
+                red_shared_add(a + 12 * kHomeField, __float_as_int(fmaf(q3, ww, kMagic)) - kMagicBits);
             }
         }
     }
@@ -1058,11 +1062,31 @@ k_deposit_home(const Record<float> *__restrict__ rec, const uint32_t *__restrict
         __syncthreads();
         int qn = 0;  // warp-uniform queue length
         const int xl = lane >> 4, cz = lane & 15;
-        for (int blk = warp; blk < kHomeT * kHomeT / 2; blk += kHomeNW) {
+        constexpr int kBlocks = kHomeT * kHomeT / 2;
+        // loads run ahead: the offsets two blocks ahead, the first record one block ahead
+        auto cell_range = [&](int blk, uint32_t &b, uint32_t &e) {
+            if (blk >= kBlocks) {
+                b = e = 0;
+                return;
+            }
             const int cy = blk & 15, cx = 2 * (blk >> 4) + xl;
             const int64_t key = (static_cast<int64_t>(t0 + cx) * ng + (t1 + cy)) * ng + (t2 + cz);
-            const uint32_t beg = offsets[key], end = offsets[key + 1];
-            if (end > beg) home_particle(acc, rec[beg], cx, cy, cz, sc0, sc1, sc2, sc3);
+            b = offsets[key];
+            e = offsets[key + 1];
+        };
+        uint32_t beg1, end1, beg2, end2;
+        cell_range(warp, beg1, end1);
+        cell_range(warp + kHomeNW, beg2, end2);
+        Record<float> r1{};
+        if (end1 > beg1) r1 = rec[beg1];
+        for (int blk = warp; blk < kBlocks; blk += kHomeNW) {
+            const int cy = blk & 15, cx = 2 * (blk >> 4) + xl;
+            const uint32_t beg = beg1, end = end1;
+            const Record<float> r = r1;
+            beg1 = beg2, end1 = end2;
+            if (end1 > beg1) r1 = rec[beg1];
+            cell_range(blk + 2 * kHomeNW, beg2, end2);
+            if (end > beg) home_particle(acc, r, cx, cy, cz, sc0, sc1, sc2, sc3);
             uint32_t next = beg + 1, extra = end > beg ? end - beg - 1 : 0u;
             while (__any_sync(0xffffffffu, extra > 0u)) {
                 const bool has = extra > 0u;
@@ -1245,15 +1269,25 @@ void deposit_tile_shape(int tile, int prec, int dims[3])
     for (int a = 0; a < 3; ++a) dims[a] = kTiles[tile].d[a];
 }
 
+// The key table: counts at C = P + 4 words (P = scratch + off_counts; 16-byte aligned
+// for the scan's vector accesses). The histogram counts into C[key], the scan turns the
+// counts into exclusive offsets in place, and the scatter advances C[key] once per
+// particle it places, leaving C[key] = offset[key + 1]. P[3] stays zero, so C - 1 is the
+// table offset[0..nkeys] the deposit reads.
+size_t key_table_bytes(int64_t nkeys) { return static_cast<size_t>(nkeys + 5) * sizeof(uint32_t); }
+uint32_t *key_table(const AssignPlan &pl, void *scratch)
+{
+    return reinterpret_cast<uint32_t *>(static_cast<char *>(scratch) + pl.off_counts) + 4;
+}
+
 cudaError_t launch_hist_moments(const pkmom_catalog &cat, const AssignPlan &pl, double box_L, void *scratch,
                                 int *err_flag, cudaStream_t s, LaunchStats &st)
 {
     char *sc = static_cast<char *>(scratch);
-    auto *counts = reinterpret_cast<uint32_t *>(sc + pl.off_counts);
-    auto *ranks = reinterpret_cast<uint32_t *>(sc + pl.off_ranks);
+    uint32_t *counts = key_table(pl, scratch);
     auto *partials = reinterpret_cast<double *>(sc + pl.off_partials);
     auto *qmax = reinterpret_cast<unsigned *>(sc + pl.off_qmax);
-    cudaError_t e = cudaMemsetAsync(counts, 0, static_cast<size_t>(pl.nkeys + 1) * sizeof(uint32_t), s);
+    cudaError_t e = cudaMemsetAsync(sc + pl.off_counts, 0, key_table_bytes(pl.nkeys), s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(qmax, 0, 4 * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
@@ -1262,11 +1296,11 @@ cudaError_t launch_hist_moments(const pkmom_catalog &cat, const AssignPlan &pl, 
         k_hist_moments<float><<<pl.hist_blocks, kHistThreads, 0, s>>>(
             tp<float>(cat.x), tp<float>(cat.y), tp<float>(cat.z), tp<float>(cat.vx), tp<float>(cat.vy),
             tp<float>(cat.vz), tp<float>(cat.mass), cat.stride, cat.n, static_cast<float>(scale), pl.ng, pl.sshift,
-            counts, ranks, partials, qmax, err_flag);
+            counts, partials, qmax, err_flag);
     } else {
         k_hist_moments<double><<<pl.hist_blocks, kHistThreads, 0, s>>>(
             tp<double>(cat.x), tp<double>(cat.y), tp<double>(cat.z), tp<double>(cat.vx), tp<double>(cat.vy),
-            tp<double>(cat.vz), tp<double>(cat.mass), cat.stride, cat.n, scale, pl.ng, pl.sshift, counts, ranks,
+            tp<double>(cat.vz), tp<double>(cat.mass), cat.stride, cat.n, scale, pl.ng, pl.sshift, counts,
             partials, qmax, err_flag);
     }
     st.launches++;
@@ -1286,7 +1320,7 @@ cudaError_t launch_moments_final(const AssignPlan &pl, int64_t n, void *scratch,
 cudaError_t launch_scan(const AssignPlan &pl, void *scratch, cudaStream_t s, LaunchStats &st)
 {
     char *sc = static_cast<char *>(scratch);
-    auto *counts = reinterpret_cast<uint32_t *>(sc + pl.off_counts);
+    uint32_t *counts = key_table(pl, scratch);
     auto *bsum = reinterpret_cast<uint32_t *>(sc + pl.off_blocksums);
     const unsigned nb = static_cast<unsigned>(pl.scan_blocks);
     k_scan_reduce<<<nb, kScanThreads, 0, s>>>(counts, pl.nkeys, bsum);
@@ -1300,21 +1334,20 @@ cudaError_t launch_scatter(const pkmom_catalog &cat, const AssignPlan &pl, doubl
                            cudaStream_t s, LaunchStats &st)
 {
     char *sc = static_cast<char *>(scratch);
-    auto *offsets = reinterpret_cast<const uint32_t *>(sc + pl.off_counts);
-    auto *ranks = reinterpret_cast<const uint32_t *>(sc + pl.off_ranks);
+    uint32_t *cursor = key_table(pl, scratch);
     const double scale = static_cast<double>(pl.ng) / box_L;
     const unsigned blocks = pl.hist_blocks;
     if (pl.prec == PKMOM_F32) {
         k_scatter<float><<<blocks, 256, 0, s>>>(tp<float>(cat.x), tp<float>(cat.y), tp<float>(cat.z),
                                                 tp<float>(cat.vx), tp<float>(cat.vy), tp<float>(cat.vz),
                                                 tp<float>(cat.mass), cat.stride, cat.n, static_cast<float>(scale),
-                                                pl.ng, pl.sshift, offsets, ranks,
+                                                pl.ng, pl.sshift, cursor,
                                                 reinterpret_cast<Record<float> *>(sc + pl.off_records));
     } else {
         k_scatter<double><<<blocks, 256, 0, s>>>(tp<double>(cat.x), tp<double>(cat.y), tp<double>(cat.z),
                                                  tp<double>(cat.vx), tp<double>(cat.vy), tp<double>(cat.vz),
                                                  tp<double>(cat.mass), cat.stride, cat.n, scale, pl.ng, pl.sshift,
-                                                 offsets, ranks,
+                                                 cursor,
                                                  reinterpret_cast<Record<double> *>(sc + pl.off_records));
     }
     st.launches++;
@@ -1324,7 +1357,7 @@ cudaError_t launch_scatter(const pkmom_catalog &cat, const AssignPlan &pl, doubl
 cudaError_t launch_deposit(const AssignPlan &pl, void *scratch, void *grids, cudaStream_t s, LaunchStats &st)
 {
     char *sc = static_cast<char *>(scratch);
-    auto *offsets = reinterpret_cast<const uint32_t *>(sc + pl.off_counts);
+    const uint32_t *offsets = key_table(pl, scratch) - 1;  // offset[0..nkeys] after the scatter
     auto *qmax = reinterpret_cast<const unsigned *>(sc + pl.off_qmax);
     const void *rec = sc + pl.off_records;
     float *halo = pl.off_halo ? reinterpret_cast<float *>(sc + pl.off_halo) : nullptr;

@@ -162,9 +162,7 @@ AssignPlan plan_assign(const pkmom_params &p, int64_t n, int num_sms, int tile_o
     const size_t rec = p.precision == PKMOM_F32 ? 32 : 64;
     size_t off = 0;
     pl.off_counts = off;
-    off = align_up(off + size_t(pl.nkeys + 1) * 4);
-    pl.off_ranks = off;
-    off = align_up(off + size_t(n) * 4);
+    off = align_up(off + key_table_bytes(pl.nkeys));
     pl.off_records = off;
     off = align_up(off + size_t(n) * rec);
     pl.off_partials = off;

@@ -34,7 +34,7 @@ struct AssignPlan {
     int list_cap = 0;        // shared-memory particle list of an FP32 deposit tile (0 = none)
     int hist_blocks = 0;     // blocks of the moments+histogram kernel
     int64_t scan_blocks = 0; // blocks of the key scan
-    size_t off_counts = 0, off_ranks = 0, off_records = 0, off_partials = 0, off_blocksums = 0, off_qmax = 0;
+    size_t off_counts = 0, off_records = 0, off_partials = 0, off_blocksums = 0, off_qmax = 0;
     size_t off_halo = 0;     // home-tile deposit: per-tile halo nodes (0 = not used)
     size_t total = 0;
 };
@@ -52,6 +52,8 @@ cudaError_t launch_scan(const AssignPlan &pl, void *scratch, cudaStream_t s, Lau
 cudaError_t launch_scatter(const pkmom_catalog &cat, const AssignPlan &pl, double box_L, void *scratch,
                            cudaStream_t s, LaunchStats &st);
 cudaError_t launch_deposit(const AssignPlan &pl, void *scratch, void *grids, cudaStream_t s, LaunchStats &st);
+// bytes of the key table (counts, then offsets) for nkeys sort keys
+size_t key_table_bytes(int64_t nkeys);
 // Tile shapes the deposit kernel is instantiated for (x, y, z nodes).
 // Tile kHomeTile (16^3, FP32) deposits each particle once in the tile owning its cell
 // (cubic order; it needs home_halo_bytes of scratch); other orders use the 16^3 gather.
@@ -66,6 +68,7 @@ struct SpectraTables {
     double umin = 0, umax = 0;
     int nsq_max = 0;
     uint16_t *bintab = nullptr;  // [nsq_max + 1] shell of |n|^2, 0xFFFF outside
+    int *thresh = nullptr;       // [nbins + 1] shell b: thresh[b] <= |n|^2 < thresh[b + 1]
     void *g_full = nullptr;      // [ng] 1/Bhat^2 per full axis (T = float or double)
     void *g_half = nullptr;      // [ng/2+1]
     double *h_full = nullptr;    // [ng] Sigma/Bhat^2 (FP64), for the mode tables

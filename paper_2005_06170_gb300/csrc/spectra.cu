@@ -137,54 +137,122 @@ k_bin(const Cx<T> *__restrict__ F, int64_t gstride, int ng, uint32_t nmodes, con
     for (int k = threadIdx.x; k < kBinVals * nbins; k += blockDim.x) out[k] = s_bins[k];
 }
 
-// Shell-major binning. Work item (n0, b): all modes of shell b in the slab n_x = n0.
-// Items are ordered slab-major, so the items running together read the same slab
-// (which stays in L2). A lane takes one row (n0, n1) at a time and walks the short
-// l-interval where the row crosses the shell (bounds from FP32 square roots widened
-// by one; membership is decided exactly by the shell table), summing the seven
-// per-mode values with Kahan-compensated FP32 adds. One FP64 warp reduction per item
-// writes partials[item][kBinVals]; k_reduce_items adds the items of each shell in a
-// fixed order.
-template <typename T>
-__global__ void __launch_bounds__(kBinThreads, 5)
-k_bin_shells(const Cx<T> *__restrict__ F, int64_t gstride, int ng, int nbins, float umin, float du,
-             const uint16_t *__restrict__ bintab, int nsq_max, const T *__restrict__ gf, const T *__restrict__ gh,
-             const double *__restrict__ mom, double *__restrict__ partials)
+// Warp sum of the lanes' values hi + lo, returned as FP64 (the same on every lane, fixed
+// butterfly order). For FP32 the partial sums are carried as unevaluated pairs of
+// floats with error-free two-sums at each level (FP64 adds are scarce on this part);
+// for FP64 plain adds.
+__device__ __forceinline__ double warp_sum_pair(float hi, float lo)
 {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float bh = __shfl_xor_sync(0xffffffffu, hi, o), bl = __shfl_xor_sync(0xffffffffu, lo, o);
+        const float sh = __fadd_rn(hi, bh);  // two-sum: sh + se = hi + bh exactly
+        const float bb = __fsub_rn(sh, hi);
+        const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(sh, bb)), __fsub_rn(bh, bb));
+        const float t = __fadd_rn(se, __fadd_rn(lo, bl));
+        hi = __fadd_rn(sh, t);  // renormalise
+        lo = __fsub_rn(t, __fsub_rn(hi, sh));
+    }
+    return static_cast<double>(hi) + static_cast<double>(lo);
+}
+__device__ __forceinline__ double warp_sum_pair(double hi, double lo)
+{
+    double v = hi + lo;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// floor(sqrt(x)) for 0 <= x < 2^24, exact
+__device__ __forceinline__ int isqrt_floor(int x)
+{
+    int r = static_cast<int>(sqrtf(static_cast<float>(x)));
+    while (r * r > x) --r;
+    while ((r + 1) * (r + 1) <= x) ++r;
+    return r;
+}
+
+// Shell-major binning. Work item (n0, b): all modes of shell b in the slab n_x = n0,
+// one warp per item, so each lane keeps one set of sums for the whole item. Items are
+// ordered slab-major, so the items running together read the same slab (which stays
+// in L2). The shell is the integer interval thresh[b] <= |n|^2 < thresh[b + 1]; in each
+// row (n0, n1) its modes form one run of l, found with exact integer square roots (no
+// mode is tested against a table). The runs of 32 rows are laid end to end and the
+// warp walks the joined list 32 modes at a time (lane j takes the j-th mode), so all
+// lanes work and consecutive lanes read consecutive modes of a row. The seven per-mode
+// values are summed with Kahan-compensated adds in the grid precision; one warp
+// reduction per item (float pairs for FP32) writes partials[item][kBinVals] in FP64, and
+// k_reduce_items adds the items of each shell in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(kBinThreads, sizeof(T) == 4 ? 4 : 2)
+k_bin_shells(const Cx<T> *__restrict__ F, int64_t gstride, int ng, int nbins, const int *__restrict__ thresh,
+             const T *__restrict__ gf, const T *__restrict__ gh, const double *__restrict__ mom,
+             double *__restrict__ partials)
+{
+    constexpr int NW = kBinThreads / 32;
+    __shared__ int s_lo[NW][32], s_pre[NW][32], s_n1[NW][32];
+    __shared__ int64_t s_row[NW][32];
+    __shared__ T s_g[NW][32];
     const int nh = ng / 2 + 1;
     const double Mtot = mom[0];
     const T vb0 = static_cast<T>(mom[2] / Mtot), vb1 = static_cast<T>(mom[3] / Mtot), vb2 = static_cast<T>(mom[4] / Mtot);
-    const int lane = threadIdx.x & 31;
-    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nwarps = gridDim.x * NW;
     const int nitems = ng * nbins;
-    for (int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < nitems; item += nwarps) {
+    for (int item = blockIdx.x * NW + w; item < nitems; item += nwarps) {
         const int b = item % nbins;
-        const int n0 = item / nbins - ng / 2;
-        const int i0 = n0 < 0 ? n0 + ng : n0;
-        const float elo = umin + b * du, ehi = umin + (b + 1) * du;
+        const int i0 = item / nbins;
+        const int n0 = i0 < ng / 2 ? i0 : i0 - ng;
+        const int lo2 = thresh[b], hi2 = thresh[b + 1];  // lo2 <= |n|^2 < hi2
         T s[kBinVals], c[kBinVals];
 #pragma unroll
         for (int k = 0; k < kBinVals; ++k) s[k] = T(0), c[k] = T(0);
-        const float rem = (ehi + 1.f) * (ehi + 1.f) - static_cast<float>(n0 * n0);
-        if (rem >= 0.f) {
-            const int R1 = static_cast<int>(floorf(sqrtf(rem)));
+        const int rem = hi2 - 1 - n0 * n0;
+        if (hi2 > lo2 && rem >= 0) {
+            const int R1 = isqrt_floor(rem);
             const int n1lo = max(-ng / 2, -R1), n1hi = min(ng / 2 - 1, R1);
             const T g0 = gf[i0];
-            for (int n1 = n1lo + lane; n1 <= n1hi; n1 += 32) {
-                const int r2 = n0 * n0 + n1 * n1;
-                const int i1 = n1 < 0 ? n1 + ng : n1;
-                const float a = elo * elo - static_cast<float>(r2), z = ehi * ehi - static_cast<float>(r2);
-                const int lo = max(0, static_cast<int>(ceilf(sqrtf(fmaxf(a, 0.f)))) - 1);
-                const int hi = min(nh - 1, static_cast<int>(floorf(sqrtf(fmaxf(z, 0.f)))) + 1);
-                const int64_t rowbase = (static_cast<int64_t>(i0) * ng + i1) * nh;
-                const T gxy = g0 * gf[i1];
-                for (int l = lo; l <= hi; ++l) {
-                    const int nsq = r2 + l * l;
-                    if (nsq > nsq_max || static_cast<int>(bintab[nsq]) != b) continue;
-                    const T g = gxy * gh[l] * ((l == 0 || l == nh - 1) ? T(1) : T(2));
-                    const int64_t mi = rowbase + l;
+            for (int r0 = n1lo; r0 <= n1hi; r0 += 32) {
+                const int n1 = r0 + lane;
+                const bool row = n1 <= n1hi;
+                int l_lo = 0, len = 0;
+                if (row) {
+                    const int r2 = n0 * n0 + n1 * n1;
+                    const int top = hi2 - 1 - r2;  // l^2 <= top
+                    if (top >= 0) {
+                        const int lh = min(isqrt_floor(top), nh - 1);
+                        const int need = lo2 - r2;  // l^2 >= need
+                        const int ll = need <= 0 ? 0 : isqrt_floor(need - 1) + 1;
+                        if (lh >= ll) l_lo = ll, len = lh - ll + 1;
+                    }
+                }
+                int inc = len;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, inc, d);
+                    if (lane >= d) inc += t;
+                }
+                const int total = __shfl_sync(0xffffffffu, inc, 31);
+                if (total == 0) continue;
+                const int i1 = row ? (n1 < 0 ? n1 + ng : n1) : 0;
+                s_lo[w][lane] = l_lo;
+                s_pre[w][lane] = inc - len;
+                s_n1[w][lane] = n1;
+                s_row[w][lane] = (static_cast<int64_t>(i0) * ng + i1) * nh;
+                s_g[w][lane] = row ? g0 * gf[i1] : T(0);
+                __syncwarp();
+                for (int m = lane; m < total; m += 32) {
+                    // the row holding the m-th mode: the last row starting at or before m
+                    // (an empty row starts where the next one does, which is then taken)
+                    int j = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1)
+                        if (s_pre[w][j + step] <= m) j += step;
+                    const int l = s_lo[w][j] + (m - s_pre[w][j]);
+                    const int64_t mi = s_row[w][j] + l;
+                    const T g = s_g[w][j] * gh[l] * ((l == 0 || l == nh - 1) ? T(1) : T(2));
                     const Cx<T> d = F[mi], p0 = F[gstride + mi], p1 = F[2 * gstride + mi], p2 = F[3 * gstride + mi];
-                    const T fn0 = static_cast<T>(n0), fn1 = static_cast<T>(n1), fn2 = static_cast<T>(l);
+                    const T fn0 = static_cast<T>(n0), fn1 = static_cast<T>(s_n1[w][j]), fn2 = static_cast<T>(l);
                     const T kr = fn0 * p0.x + fn1 * p1.x + fn2 * p2.x;
                     const T ki = fn0 * p0.y + fn1 * p1.y + fn2 * p2.y;
                     const Cx<T> q0{p0.x - vb0 * d.x, p0.y - vb0 * d.y};
@@ -208,13 +276,12 @@ k_bin_shells(const Cx<T> *__restrict__ F, int64_t gstride, int ng, int nbins, fl
                         s[k] = t;
                     }
                 }
+                __syncwarp();
             }
         }
 #pragma unroll
         for (int k = 0; k < kBinVals; ++k) {
-            double dsum = static_cast<double>(s[k]) - static_cast<double>(c[k]);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+            const double dsum = warp_sum_pair(s[k], -c[k]);
             if (lane == 0) partials[static_cast<int64_t>(item) * kBinVals + k] = dsum;
         }
     }
@@ -439,6 +506,7 @@ cudaError_t upload(void **dst, const std::vector<T> &src)
 void free_spectra_tables(SpectraTables &t)
 {
     cudaFree(t.bintab);
+    cudaFree(t.thresh);
     cudaFree(t.g_full);
     cudaFree(t.g_half);
     cudaFree(t.h_full);
@@ -481,8 +549,20 @@ cudaError_t build_spectra_tables(SpectraTables &t, int ng, int order, int nbins,
         ghd[i] = 1.0 / bhat2(w, order);
         hhd[i] = sigma_m(w, order) / bhat2(w, order);
     }
+    // shell b is the interval thresh[b] <= |n|^2 < thresh[b + 1] (bins are monotone in |n|^2)
+    std::vector<int> thresh(nbins + 1, t.nsq_max + 1);
+    int last = 0;
+    for (int nsq = t.nsq_max; nsq >= 1; --nsq) {
+        const int b = bintab[nsq];
+        if (b == 0xffff) continue;
+        if (!last) last = nsq;
+        for (int k = b; k >= 0 && thresh[k] > nsq; --k) thresh[k] = nsq;
+    }
+    thresh[nbins] = last + 1;
+    for (int k = nbins - 1; k >= 0; --k) thresh[k] = std::min(thresh[k], thresh[k + 1]);
     cudaError_t e;
     if ((e = upload(reinterpret_cast<void **>(&t.bintab), bintab)) != cudaSuccess) return e;
+    if ((e = upload(reinterpret_cast<void **>(&t.thresh), thresh)) != cudaSuccess) return e;
     if (prec == PKMOM_F32) {
         std::vector<float> gf(gfd.begin(), gfd.end()), gh(ghd.begin(), ghd.end());
         if ((e = upload(&t.g_full, gf)) != cudaSuccess) return e;
@@ -557,17 +637,15 @@ cudaError_t launch_bin_shells(const SpectraTables &t, const void *grids, const d
 {
     const int ng = t.ng, nh = ng / 2 + 1;
     const int64_t gstride = static_cast<int64_t>(ng) * ng * nh;
-    const float du = static_cast<float>((t.umax - t.umin) / t.nbins);
     const unsigned blocks = static_cast<unsigned>(t.shell_blocks);
     if (t.prec == PKMOM_F32)
         k_bin_shells<float><<<blocks, kBinThreads, 0, s>>>(
-            static_cast<const Cx<float> *>(grids), gstride, ng, t.nbins, static_cast<float>(t.umin), du, t.bintab,
-            t.nsq_max, static_cast<const float *>(t.g_full), static_cast<const float *>(t.g_half), moments_dev,
-            t.item_partials);
+            static_cast<const Cx<float> *>(grids), gstride, ng, t.nbins, t.thresh,
+            static_cast<const float *>(t.g_full), static_cast<const float *>(t.g_half), moments_dev, t.item_partials);
     else
         k_bin_shells<double><<<blocks, kBinThreads, 0, s>>>(
-            static_cast<const Cx<double> *>(grids), gstride, ng, t.nbins, static_cast<float>(t.umin), du, t.bintab,
-            t.nsq_max, static_cast<const double *>(t.g_full), static_cast<const double *>(t.g_half), moments_dev,
+            static_cast<const Cx<double> *>(grids), gstride, ng, t.nbins, t.thresh,
+            static_cast<const double *>(t.g_full), static_cast<const double *>(t.g_half), moments_dev,
             t.item_partials);
     double *sums = t.mode_sums + static_cast<size_t>(kModeVals) * t.nbins;
     k_reduce_items<kBinVals><<<t.nbins, 256, 0, s>>>(t.item_partials, ng, t.nbins, sums);
