@@ -47,6 +47,14 @@ WORKLOADS = {
                             1024, 128, "f32"),
 }
 DEFAULT = "zeldovich256_ng256"
+# DRAM bytes (read + write) per launch of the dominant stage's kernels, from one ncu
+# capture of the current kernels (profiles/kernels_zeldovich256_ng256.md); a stage
+# whose kernels change drops its entry until it is captured again
+MEASURED_TRAFFIC = {
+    ("zeldovich256_ng256", "deposit"): ((617.737984 + 409.859328 + 453.298688 + 164.873472) * 1e6,
+                                        "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_deposit_home and "
+                                        "k_home_fixup, one launch each (profiles/kernels_zeldovich256_ng256.md)"),
+}
 # configs 4 and 5 run through their own drivers below
 MULTI = {
     "batch64": "64 catalogues in one launch sequence: particle counts log-uniform in [1e5, 2e7], seeded "
@@ -421,10 +429,15 @@ def main(argv=None):
         "final": 0,
     }[dom]
     achieved = alg_bytes / (stage_ms[dom] * 1e-3) / 1e9 if stage_ms[dom] > 0 else None
-    roof = {"kernel": {"deposit": "k_deposit", "bin": "k_bin", "hist": "k_hist_moments", "scatter": "k_scatter",
-                       "scan": "k_scan_*", "final": "k_finalize"}[dom],
+    home = prec == "f32" and ng % 16 == 0 and n >= ng ** 3 / 2  # the library's home-tile deposit
+    deposit_kernels = "k_deposit_home + k_home_fixup" if home else "k_deposit_fx"
+    traffic = MEASURED_TRAFFIC.get((args.workload, dom))
+    roof = {"kernel": {"deposit": deposit_kernels, "bin": "k_bin_shells + k_reduce_items", "hist": "k_hist_moments",
+                       "scatter": "k_scatter", "scan": "k_scan_*", "final": "k_finalize"}[dom],
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": traffic[0] if traffic else None,
+            "traffic_source": traffic[1] if traffic else None,
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
             "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": stage_ms[dom]}
 
