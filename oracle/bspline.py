@@ -27,6 +27,8 @@ from __future__ import annotations
 import math
 from fractions import Fraction
 
+import functools
+
 import numpy as np
 
 
@@ -114,6 +116,7 @@ def phi_alias_sum_brute(w, m: int = 4, jmax: int = 200):
     return (phi_hat(w[..., None] + 2.0 * np.pi * J, m) ** 2).sum(axis=-1)
 
 
+@functools.lru_cache(maxsize=None)
 def bl_coefficients(m: int = 4, nmax: int = 40, nquad: int = 4096):
     """Coefficients c_n of phi(x) = sum_n c_n B_m(x - n), n = -nmax..nmax.
 

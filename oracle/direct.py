@@ -3,8 +3,11 @@
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
 * deposit_bl_direct - real-space assignment with the orthonormalised scaling
-  function phi itself (tabulated from its B-spline expansion), summed over periodic
-  images, no Fourier-space factor. Pins the factored form used by estimator.py.
+  function phi itself (from its B-spline expansion), summed over periodic images, no
+  Fourier-space factor. Untruncated it pins the factored form used by estimator.py;
+  with a radius R it is the oracle of the direct truncated BL assignment (phi set to
+  zero beyond R cells, the literal real-space stencil of Sec. 2.4.1), which
+  estimator.estimate(bl_radius=R) uses.
 * dft3           - O(M^2) discrete Fourier transform by its definition.
 * full_sphere_bins - binning over every mode of a full complex FFT (no half-spectrum
   weights), using the same bin definition.
@@ -16,31 +19,39 @@ import numpy as np
 from . import bspline as _bs
 
 
-def _folded_weights(x: float, ng: int, order: int, reach: int, nmax: int) -> np.ndarray:
-    """Weights phi(x - n) for all integer n within `reach`, folded onto ng periodic nodes."""
-    base = int(np.floor(x))
-    nodes = np.arange(base - reach, base + reach + 1)
-    w = _bs.phi(x - nodes, order, nmax=nmax)
-    out = np.zeros(ng)
-    np.add.at(out, np.mod(nodes, ng), w)
+def _folded_weights(x: np.ndarray, ng: int, order: int, reach: int, nmax: int, radius: float | None) -> np.ndarray:
+    """Weights phi(x_j - n) for all integer n within `reach` of each x_j, zero where
+    |x_j - n| >= radius (if given), folded onto ng periodic nodes: (len(x), ng)."""
+    x = np.asarray(x, dtype=np.float64)
+    base = np.floor(x).astype(np.int64)
+    nodes = base[:, None] + np.arange(-reach, reach + 1)[None, :]
+    d = x[:, None] - nodes
+    w = _bs.phi(d, order, nmax=nmax)
+    if radius is not None:
+        w = np.where(np.abs(d) < radius, w, 0.0)
+    out = np.zeros((len(x), ng))
+    rows = np.repeat(np.arange(len(x)), nodes.shape[1])
+    np.add.at(out, (rows, np.mod(nodes, ng).ravel()), w.ravel())
     return out
 
 
 def deposit_bl_direct(u: np.ndarray, q: np.ndarray, ng: int, order: int = 4,
-                      reach: int = 40, nmax: int = 40) -> np.ndarray:
-    """Grid G_f(n) = sum_j q_jf sum_images phi(u_j - n) (separable product), FP64."""
+                      reach: int = 40, nmax: int = 40, radius: float | None = None) -> np.ndarray:
+    """Grid G_f(n) = sum_j q_jf sum_images phi_R(u_j - n) (separable product), FP64,
+    with phi_R = phi truncated to |x| < radius (no truncation if radius is None)."""
     u = np.asarray(u, dtype=np.float64)
     q = np.asarray(q, dtype=np.float64)
     if q.ndim == 1:
         q = q[:, None]
+    if radius is not None:
+        reach = int(np.ceil(radius)) + 1
     grids = np.zeros((q.shape[1], ng, ng, ng))
-    for j in range(len(u)):
-        wx = _folded_weights(u[j, 0], ng, order, reach, nmax)
-        wy = _folded_weights(u[j, 1], ng, order, reach, nmax)
-        wz = _folded_weights(u[j, 2], ng, order, reach, nmax)
-        cube = wx[:, None, None] * wy[None, :, None] * wz[None, None, :]
-        for f in range(q.shape[1]):
-            grids[f] += q[j, f] * cube
+    for j0 in range(0, len(u), 512):
+        sl = slice(j0, j0 + 512)
+        wx = _folded_weights(u[sl, 0], ng, order, reach, nmax, radius)
+        wy = _folded_weights(u[sl, 1], ng, order, reach, nmax, radius)
+        wz = _folded_weights(u[sl, 2], ng, order, reach, nmax, radius)
+        grids += np.einsum("jf,ja,jb,jc->fabc", q[sl], wx, wy, wz, optimize=True)
     return grids
 
 

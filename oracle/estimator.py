@@ -120,9 +120,11 @@ def spectra_from_fourier(F: np.ndarray, mom: dict, *, L: float, ng: int, order: 
                          nbins: int, kmin_kf: float = 1.0, kmax_kf: float | None = None,
                          theta_scale: float = 1.0, subtract_shot_noise: bool = True,
                          theta_sn: str = "tensor", bulk: bool = True,
-                         per_mode: bool = False) -> dict:
+                         per_mode: bool = False, bl_assigned: bool = False) -> dict:
     """Steps 4-7 on the Fourier transforms F[4] of the B-spline-deposited grids.
 
+    bl_assigned: F holds grids already assigned with the BL function itself (the direct
+    real-space deposit), so the Fourier-space factor prod Sigma^{-1/2} is not applied.
     Returns shell averages. With per_mode=True also returns the per-mode arrays
     (only sensible for small grids).
     """
@@ -155,7 +157,7 @@ def spectra_from_fourier(F: np.ndarray, mom: dict, *, L: float, ng: int, order: 
         nsq = (n0 * n0 + n1 * n1 + n2 * n2).astype(np.int64)
         b = bin_index(nsq, nbins, umin, umax) + 1  # 0 = excluded
         wmode = np.broadcast_to(wt_half[None, :], nsq.shape)
-        Cfac = C_full[i0] * C_full[:, None] * C_half[None, :]
+        Cfac = 1.0 if bl_assigned else C_full[i0] * C_full[:, None] * C_half[None, :]
         W2 = W2_full[i0] * W2_full[:, None] * W2_half[None, :]
         A = A_full[i0] * A_full[:, None] * A_half[None, :]
         kvec = [kf * n0 * np.ones_like(n1 * n2), kf * n1 * np.ones_like(n2), kf * n2 * np.ones_like(n1)]
@@ -227,17 +229,37 @@ def spectra_from_fourier(F: np.ndarray, mom: dict, *, L: float, ng: int, order: 
     return out
 
 
+def assign_bl_direct(pos, vel, mass, *, L: float, ng: int, radius: float) -> np.ndarray:
+    """Direct real-space assignment with the BL function truncated to |x| < radius cells
+    (cubic order), onto four ng^3 FP64 grids."""
+    from . import direct
+    u = grid_coordinates(np.asarray(pos), L, ng)
+    v = np.asarray(vel, dtype=np.float64)
+    m = np.ones(len(v)) if mass is None else np.asarray(mass, dtype=np.float64)
+    q = np.concatenate([m[:, None], m[:, None] * v], axis=1)
+    return direct.deposit_bl_direct(u, q, ng, 4, radius=radius)
+
+
 def estimate(pos, vel, mass=None, *, L: float, ng: int, order: int = 4, nbins: int,
              kmin_kf: float = 1.0, kmax_kf: float | None = None, theta_scale: float = 1.0,
              subtract_shot_noise: bool = True, theta_sn: str = "tensor", bulk: bool = True,
-             workers: int = -1) -> dict:
-    """The whole estimator on one catalogue: steps 1-7 of the module docstring."""
+             workers: int = -1, bl_radius: float = 0) -> dict:
+    """The whole estimator on one catalogue: steps 1-7 of the module docstring.
+
+    bl_radius > 0: step 2 with the BL function truncated to |x| < bl_radius cells and
+    deposited directly in real space (cubic order; small catalogues only)."""
     mom = moments(vel, mass)
-    grids = assign(pos, vel, mass, L=L, ng=ng, order=order)
+    if bl_radius:
+        if order != 4:
+            raise ValueError("the direct BL deposit is of cubic order")
+        grids = assign_bl_direct(pos, vel, mass, L=L, ng=ng, radius=bl_radius)
+    else:
+        grids = assign(pos, vel, mass, L=L, ng=ng, order=order)
     F = fft_grids(grids, workers=workers)
     del grids
     out = spectra_from_fourier(F, mom, L=L, ng=ng, order=order, nbins=nbins, kmin_kf=kmin_kf,
                                kmax_kf=kmax_kf, theta_scale=theta_scale,
-                               subtract_shot_noise=subtract_shot_noise, theta_sn=theta_sn, bulk=bulk)
+                               subtract_shot_noise=subtract_shot_noise, theta_sn=theta_sn, bulk=bulk,
+                               bl_assigned=bool(bl_radius))
     out["moments"] = mom
     return out
