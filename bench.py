@@ -326,6 +326,8 @@ def main(argv=None):
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(MULTI))
     ap.add_argument("--requests", type=int, default=300, help="serve: number of requests")
     ap.add_argument("--tile", type=int, default=-1, help="deposit tile id (pkmom_set_tuning); -1 = automatic")
+    ap.add_argument("--bl-radius", type=int, default=0,
+                    help="0: exact BL kernel; 2..4: the BL function truncated to that many cells, deposited directly")
     ap.add_argument("--impl", default="pkmom", choices=["pkmom", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -358,7 +360,7 @@ def main(argv=None):
     L = spec["L"]
     pos = torch.from_numpy(cat["pos"]).to(dev)
     vel = torch.from_numpy(cat["vel"]).to(dev)
-    p = pkmom.params(L, ng, nbins, precision=pkmom.F32 if prec == "f32" else pkmom.F64)
+    p = pkmom.params(L, ng, nbins, precision=pkmom.F32 if prec == "f32" else pkmom.F64, bl_radius=args.bl_radius)
     ctx = pkmom.Context(local)
     if args.tile >= 0:
         ctx.set_tuning(args.tile, -1)
@@ -430,8 +432,9 @@ def main(argv=None):
     }[dom]
     achieved = alg_bytes / (stage_ms[dom] * 1e-3) / 1e9 if stage_ms[dom] > 0 else None
     home = prec == "f32" and ng % 16 == 0 and n >= ng ** 3 / 2  # the library's home-tile deposit
-    deposit_kernels = "k_deposit_home + k_home_fixup" if home else "k_deposit_fx"
-    traffic = MEASURED_TRAFFIC.get((args.workload, dom))
+    home = home and not args.bl_radius
+    deposit_kernels = "k_deposit_home + k_home_fixup" if home else ("k_deposit_fx" if prec == "f32" else "k_deposit")
+    traffic = None if args.bl_radius else MEASURED_TRAFFIC.get((args.workload, dom))
     roof = {"kernel": {"deposit": deposit_kernels, "bin": "k_bin_shells + k_reduce_items", "hist": "k_hist_moments",
                        "scatter": "k_scatter", "scan": "k_scan_*", "final": "k_finalize"}[dom],
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -444,7 +447,9 @@ def main(argv=None):
     line = {"metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": prec, "data": "synthetic",
-            "config": {"workload": desc, "n_particles": n, "ng": ng, "nbins": nbins, "box_L": L,
+            "config": {"workload": desc + (f"; BL function truncated to {args.bl_radius} cells, direct deposit"
+                                           if args.bl_radius else ""),
+                       "n_particles": n, "ng": ng, "nbins": nbins, "box_L": L,
                        "bulk": "with and without", "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": f"inputs larger than L2: catalogue {n * 6 * elem / 1e6:.0f} MB, grids "
                              f"{4 * ng * ng * (ng + 2) * elem / 1e6:.0f} MB, no flush"},

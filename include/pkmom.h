@@ -112,6 +112,11 @@ typedef struct {
     int subtract_shot_noise; /* 1: remove the shot noise (default), 0: raw / W^2 */
     int bulk;                /* 1: also the bulk-flow-subtracted spectra (rows 6-8, 12-13) */
     int theta_sn_mode;       /* 0: exact per-mode k.Q.k noise (default), 1: isotropic sigma^2/3 */
+    int bl_radius;           /* 0: the exact BL kernel (B-spline deposit, Fourier-space factor;
+                                default). R in 2..4: the BL function truncated to |x| < R cells,
+                                deposited directly in real space (the literal stencil of
+                                Sec. 2.4.1; (2R)^3 nodes per particle), then divided by the
+                                same window W^2; order must be 4 */
 } pkmom_params;
 
 /* Catalogue moments written by pkmom_assign (device memory, 16 doubles):

@@ -16,6 +16,8 @@
 //                   shared memory, then writes each node of the tile exactly once.
 //                   No global atomics, no zero-fill pass.
 #include <cfloat>
+#include <cmath>
+#include <mutex>
 
 #include "pkmom_internal.cuh"
 
@@ -342,6 +344,35 @@ __device__ __forceinline__ void bspline_weights(T t, T (&w)[M], int &first)
     }
 }
 
+// Coefficients c_0..c_7 of the BL function phi = sum_n c_n B_4(. - n), c_{-n} = c_n
+// (cubic order), set once per device by set_bl_coefficients.
+__constant__ float c_bl_f[8];
+__constant__ double c_bl_d[8];
+template <typename T> __device__ __forceinline__ T bl_coef(int n);
+template <> __device__ __forceinline__ float bl_coef<float>(int n) { return c_bl_f[n < 0 ? -n : n]; }
+template <> __device__ __forceinline__ double bl_coef<double>(int n) { return c_bl_d[n < 0 ? -n : n]; }
+
+// Weights of the BL function truncated to |x| < R cells (the direct real-space
+// assignment of Sec. 2.4.1) for a particle at offset t in its cell: nodes floor(u) + k,
+// k = 1 - R .. R. phi(t - k) = sum_j b_j(t) c_{j-1-k} with b_j the cubic B-spline
+// weights of nodes floor(u) - 1 + j; zero where |t - k| >= R.
+template <int R, typename T>
+__device__ __forceinline__ void bl_weights(T t, T (&w)[2 * R], int &first)
+{
+    T b[4];
+    int f4;
+    bspline_weights<4, T>(t, b, f4);
+    first = 1 - R;
+#pragma unroll
+    for (int i = 0; i < 2 * R; ++i) {
+        const int k = 1 - R + i;
+        T v = T(0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v += b[j] * bl_coef<T>(j - 1 - k);
+        w[i] = fabs(t - T(k)) < T(R) ? v : T(0);
+    }
+}
+
 template <typename T, int M, int T0, int T1, int T2, int NT>
 struct DepositCfg {
     static constexpr int HL = (M % 2 == 0) ? M / 2 : (M + 1) / 2;  // cells below the tile that reach it
@@ -356,6 +387,9 @@ struct DepositCfg {
 // Largest product of three B-spline weights of order M: bounds any node value of the
 // tile by this times (particles in the tile's reach) times max |q|.
 template <int M> constexpr float kMaxWeight3 = M == 4 ? 0.2962963f : (M == 3 ? 0.421875f : 1.0f);
+// The same for the BL function: max |phi| = phi(0) = 1.0890, cubed 1.2916.
+constexpr float kMaxWeight3BL = 1.2917f;
+template <int M, int BLR> constexpr float kMaxW3 = BLR > 0 ? kMaxWeight3BL : kMaxWeight3<M>;
 
 // The particle index ranges of one tile: for every (x, y) cell row within reach of the
 // tile, the sort-key segments covering the z cells within reach (one range, or two
@@ -436,7 +470,7 @@ __device__ __forceinline__ int find_slot(const uint32_t *s_pre, uint32_t p)
 }
 
 // Weights and tile-local node indices (-1 outside the tile) of one particle.
-template <typename T, int M>
+template <typename T, int M, int BLR = 0>
 __device__ __forceinline__ void stencil(const Record<T> &r, int ng, int t0, int t1, int t2, int T0, int T1, int T2,
                                         T (&w)[3][M], int (&li)[3][M])
 {
@@ -448,7 +482,8 @@ __device__ __forceinline__ void stencil(const Record<T> &r, int ng, int t0, int 
     for (int a = 0; a < 3; ++a) {
         const int c = (packed >> (10 * a)) & 1023;
         int first;
-        bspline_weights<M, T>(t[a], w[a], first);
+        if constexpr (BLR > 0) bl_weights<BLR, T>(t[a], w[a], first);
+        else bspline_weights<M, T>(t[a], w[a], first);
 #pragma unroll
         for (int k = 0; k < M; ++k) {
             int l = c + first + k - tb[a];
@@ -458,9 +493,30 @@ __device__ __forceinline__ void stencil(const Record<T> &r, int ng, int t0, int 
     }
 }
 
+// Weight and tile-local index of x node k0 (node floor(u) + 1 - R + k0) of the truncated
+// BL stencil, formed on its own (the rolled x loop of the wide stencils); false if the
+// node lies outside the tile or beyond the radius.
+template <int R, typename T>
+__device__ __forceinline__ bool bl_node_x(const Record<T> &r, int ng, int t0, int T0, int k0, T &w, int &l)
+{
+    const int k = 1 - R + k0;
+    int lx = (unpack_cell(r.u.w) & 1023) + k - t0;
+    lx = lx < 0 ? lx + ng : (lx >= ng ? lx - ng : lx);
+    if (lx >= T0 || !(fabs(r.u.x - T(k)) < T(R))) return false;
+    T b[4];
+    int f4;
+    bspline_weights<4, T>(r.u.x, b, f4);
+    T v = T(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v += b[j] * bl_coef<T>(j - 1 - k);
+    w = v;
+    l = lx;
+    return true;
+}
+
 // Tile-gather deposit with shared-memory atomics in the grid precision (used for
 // FP64 grids, where FP64 accuracy is required).
-template <typename T, int M, int T0, int T1, int T2, int NT>
+template <typename T, int M, int T0, int T1, int T2, int NT, int BLR = 0>
 __global__ void __launch_bounds__(NT)
 k_deposit(const Record<T> *__restrict__ rec, const uint32_t *__restrict__ offsets,
           const unsigned *__restrict__ /*qmax_bits*/, int ng, int sshift, T *__restrict__ grids, int64_t grid_elems,
@@ -487,15 +543,13 @@ k_deposit(const Record<T> *__restrict__ rec, const uint32_t *__restrict__ offset
         const Record<T> r = rec[s_beg[slot] + (p - s_pre[slot])];
         T w[3][M];
         int li[3][M];
-        stencil<T, M>(r, ng, t0, t1, t2, T0, T1, T2, w, li);
-#pragma unroll
-        for (int k0 = 0; k0 < M; ++k0) {
-            if (li[0][k0] < 0) continue;
+        stencil<T, M, BLR>(r, ng, t0, t1, t2, T0, T1, T2, w, li);
+        auto plane = [&](T wx, int lx) {  // the M x M (y, z) nodes of one x node
 #pragma unroll
             for (int k1 = 0; k1 < M; ++k1) {
                 if (li[1][k1] < 0) continue;
-                const T w01 = w[0][k0] * w[1][k1];
-                const int b01 = (li[0][k0] * T1 + li[1][k1]) * T2;
+                const T w01 = wx * w[1][k1];
+                const int b01 = (lx * T1 + li[1][k1]) * T2;
 #pragma unroll
                 for (int k2 = 0; k2 < M; ++k2) {
                     if (li[2][k2] < 0) continue;
@@ -507,6 +561,17 @@ k_deposit(const Record<T> *__restrict__ rec, const uint32_t *__restrict__ offset
                     atomicAdd(a + 3 * C::TN, r.q.w * ww);
                 }
             }
+        };
+        if constexpr (BLR > 2) {  // wide stencils: rolled x loop (instruction cache)
+            T wx;
+            int lx;
+#pragma unroll 1
+            for (int k0 = 0; k0 < M; ++k0)
+                if (bl_node_x<BLR, T>(r, ng, t0, T0, k0, wx, lx)) plane(wx, lx);
+        } else {
+#pragma unroll
+            for (int k0 = 0; k0 < M; ++k0)
+                if (li[0][k0] >= 0) plane(w[0][k0], li[0][k0]);
         }
     }
     __syncthreads();
@@ -588,9 +653,11 @@ __device__ __forceinline__ void cell_chunk(const Record<float> *__restrict__ rec
     }
 }
 
-// Fixed-point scales of a tile: 2^st with (bound of any node sum) * 2^st < 2^29, and,
+// Fixed-point scales of a tile: 2^st with (bound of any node sum) * 2^st < 2^30, and,
 // for the cell-block paths, the fine scale 2^sf with (largest contribution) * 2^sf < 2^22
-// and st <= sf. Per-particle paths round at 2^min(st, sf) directly.
+// and st <= sf. Per-particle paths round at 2^min(st, sf) directly. A node's integer sum
+// is then below 2^30 plus half a unit per rounding (fewer than 2^31 particles), which
+// fits a signed 32-bit accumulator.
 __device__ __forceinline__ void tile_scales(float bound, float cmax, bool cells, float &scale, float &fine, int &shift)
 {
     int eb = 0, ec = 0;
@@ -599,7 +666,7 @@ __device__ __forceinline__ void tile_scales(float bound, float cmax, bool cells,
     if (!isfinite(bound)) eb = 150;
     if (!isfinite(cmax)) ec = 150;
     auto clampx = [](int e) { return e > 120 ? 120 : (e < -120 ? -120 : e); };
-    const int sf = clampx(22 - ec), st = clampx(min(29 - eb, 22 - ec));
+    const int sf = clampx(22 - ec), st = clampx(min(30 - eb, 22 - ec));
     scale = ldexpf(1.0f, st);
     fine = ldexpf(1.0f, sf);
     shift = cells ? min(30, sf - st) : 0;
@@ -655,7 +722,7 @@ __device__ __forceinline__ void deposit_cells_path(const Record<float> *__restri
 // padded to an odd length.
 //
 // Fixed point: field f of the tile uses the scale 2^s_f with
-//   B_f 2^s_f < 2^29,   B_f = w3 * min(M^2 * largest row count, particle count) * max |q_f|
+//   B_f 2^s_f < 2^30,   B_f = w3 * min(M^2 * largest row count, particle count) * max |q_f|
 // over the tile's reach (w3 = the largest product of three weights; a node receives from
 // at most M^2 cell rows, each contributing at most `largest row count` particles, and
 // from no more than all of them; max |q_f| over the catalogue), so no node sum can overflow, and also max |q_f| w3 2^s_f < 2^22, so that
@@ -663,7 +730,7 @@ __device__ __forceinline__ void deposit_cells_path(const Record<float> *__restri
 // nearest even, one rounding of the exact product). The bound depends only on counts
 // and maxima, and integer sums do not depend on order: the grids are the same whatever
 // order the sort leaves particles of one cell in.
-template <int M, int T0, int T1, int T2, int NT>
+template <int M, int T0, int T1, int T2, int NT, int BLR = 0>
 __global__ void __launch_bounds__(NT)
 k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__ offsets,
              const unsigned *__restrict__ qmax_bits, int ng, int sshift, float *__restrict__ grids, int64_t grid_elems,
@@ -691,10 +758,34 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
     for (int k = threadIdx.x; k < 4 * TNP; k += NT) acc[k] = 0;
     if (threadIdx.x == 0) s_rowmax = 0;
     const uint32_t total = build_ranges<C>(offsets, ng, sshift, t0, t1, t2, T2, s_beg, s_pre);
-    // largest row count: a row's two pieces are slots 2r and 2r + 1
-    for (int r = threadIdx.x; 2 * r + 1 < C::MAXR + 1; r += NT) {
-        const uint32_t c = s_pre[2 * r + 2 <= C::MAXR ? 2 * r + 2 : C::MAXR] - s_pre[2 * r];
-        if (c) atomicMax(&s_rowmax, c);
+    if (BLR > 0 && sshift == 0) {
+        // the wide BL stencil: a node receives from M consecutive cells of each of M x M
+        // cell rows, so bound with the largest count of M consecutive cells of a row
+        // (per-cell keys: each row's offsets are cumulative along z)
+        const int r0n = C::R0 < ng ? C::R0 : ng, r1n = C::R1 < ng ? C::R1 : ng;
+        const int zc = (T2 + C::HL + C::HR) < ng ? (T2 + C::HL + C::HR) : ng;
+        for (int r = threadIdx.x; r < r0n * r1n; r += NT) {
+            int a0 = t0 - C::HL + r / r1n, a1 = t1 - C::HL + r % r1n;
+            a0 = a0 < 0 ? a0 + ng : (a0 >= ng ? a0 - ng : a0);
+            a1 = a1 < 0 ? a1 + ng : (a1 >= ng ? a1 - ng : a1);
+            const int64_t base = (static_cast<int64_t>(a0) * ng + a1) * ng;
+            uint32_t best = 0;
+            for (int w0 = 0; w0 + M <= zc; ++w0) {
+                int z = t2 - C::HL + w0;
+                z = z < 0 ? z + ng : (z >= ng ? z - ng : z);
+                const uint32_t c = z + M <= ng ? offsets[base + z + M] - offsets[base + z]
+                                               : (offsets[base + ng] - offsets[base + z]) +
+                                                     (offsets[base + z + M - ng] - offsets[base]);
+                best = c > best ? c : best;
+            }
+            if (best) atomicMax(&s_rowmax, best);
+        }
+    } else {
+        // largest row count: a row's two pieces are slots 2r and 2r + 1
+        for (int r = threadIdx.x; 2 * r + 1 < C::MAXR + 1; r += NT) {
+            const uint32_t c = s_pre[2 * r + 2 <= C::MAXR ? 2 * r + 2 : C::MAXR] - s_pre[2 * r];
+            if (c) atomicMax(&s_rowmax, c);
+        }
     }
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -721,7 +812,7 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
     // dense tiles (cubic order, more than two particles per reach cell on average) sum
     // each cell's particles in registers first (cell-block path below)
     constexpr int NREACH = C::R0 * C::R1 * (T2 + C::HL + C::HR);
-    const bool dense = M == 4 && total > 2u * NREACH && sshift == 0 && ng >= C::R0 && ng >= C::R1 &&
+    const bool dense = M == 4 && BLR == 0 && total > 2u * NREACH && sshift == 0 && ng >= C::R0 && ng >= C::R1 &&
                        ng >= T2 + C::HL + C::HR;
     // per-field scale from order-independent bounds only (so that the grids, and the
     // spectra, do not depend on the order in which sorted particles share a cell)
@@ -729,7 +820,7 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
     if (threadIdx.x < 4) {
         const int f = threadIdx.x;
         const float m = __uint_as_float(qmax_bits[f]);  // max |q_f| over the catalogue
-        const float w3 = kMaxWeight3<M> * 1.0001f;
+        const float w3 = kMaxW3<M, BLR> * 1.0001f;
         const float reach = fminf(static_cast<float>(M * M) * static_cast<float>(s_rowmax), static_cast<float>(total));
         tile_scales(w3 * reach * m, w3 * m, dense, s_scale[f], s_fine[f], s_shift[f]);
     }
@@ -739,7 +830,7 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
     constexpr int kMagicBits = 0x4B400000;
 
     bool cells_done = false;
-    if constexpr (M == 4) {
+    if constexpr (M == 4 && BLR == 0) {  // the cell-block path uses B-spline pieces
         if (dense) {
             deposit_cells_path<T0, T1, T2, NT>(rec, offsets, ng, t0, t1, t2, acc, TNP, RW, s_fine, s_shift);
             cells_done = true;
@@ -752,16 +843,15 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
             const Record<float> rc = rec[record_index(p, slot)];
             float w[3][M];
             int li[3][M];
-            stencil<float, M>(rc, ng, t0, t1, t2, T0, T1, T2, w, li);
+            stencil<float, M, BLR>(rc, ng, t0, t1, t2, T0, T1, T2, w, li);
             const float q0 = rc.q.x * sc0, q1 = rc.q.y * sc1, q2 = rc.q.z * sc2, q3 = rc.q.w * sc3;
-#pragma unroll
-            for (int k0 = 0; k0 < M; ++k0) {
-                if (li[0][k0] < 0) continue;
+            // the M x M (y, z) nodes of one x node
+            auto plane = [&](float wx, int lx) {
 #pragma unroll
                 for (int k1 = 0; k1 < M; ++k1) {
                     if (li[1][k1] < 0) continue;
-                    const float w01 = w[0][k0] * w[1][k1];
-                    const int b01 = (li[0][k0] * T1 + li[1][k1]) * RW;
+                    const float w01 = wx * w[1][k1];
+                    const int b01 = (lx * T1 + li[1][k1]) * RW;
 #pragma unroll
                     for (int k2 = 0; k2 < M; ++k2) {
                         if (li[2][k2] < 0) continue;
@@ -773,6 +863,19 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
                         atomicAdd(a + 3 * TNP, __float_as_int(fmaf(q3, ww, kMagic)) - kMagicBits);
                     }
                 }
+            };
+            if constexpr (BLR > 2) {
+                // wide stencils: a rolled loop over x nodes keeps the code in the
+                // instruction cache; each x weight is formed where it is used
+                float wx;
+                int lx;
+#pragma unroll 1
+                for (int k0 = 0; k0 < M; ++k0)
+                    if (bl_node_x<BLR, float>(rc, ng, t0, T0, k0, wx, lx)) plane(wx, lx);
+            } else {
+#pragma unroll
+                for (int k0 = 0; k0 < M; ++k0)
+                    if (li[0][k0] >= 0) plane(w[0][k0], li[0][k0]);
             }
         }
     }
@@ -1194,7 +1297,7 @@ constexpr TileDesc kTiles[] = {
     {PKMOM_F32, {16, 16, 16}},  // 7: home tiles (cubic order; other orders use tile 0)
 };
 
-template <typename T, int M, int T0, int T1, int T2, int NT>
+template <typename T, int M, int T0, int T1, int T2, int NT, int BLR = 0>
 cudaError_t launch_deposit_t(const AssignPlan &pl, const uint32_t *offsets, const unsigned *qmax, const Record<T> *rec,
                              void *grids, cudaStream_t s)
 {
@@ -1203,11 +1306,11 @@ cudaError_t launch_deposit_t(const AssignPlan &pl, const uint32_t *offsets, cons
     size_t smem = C::smem;
     int list_cap = 0;
     if constexpr (sizeof(T) == 4) {
-        kern = k_deposit_fx<M, T0, T1, T2, NT>;
+        kern = k_deposit_fx<M, T0, T1, T2, NT, BLR>;
         list_cap = pl.list_cap;
         smem = size_t(4) * T0 * T1 * (T2 + 1) * sizeof(int) + size_t(list_cap) * sizeof(uint32_t);
     } else {
-        kern = k_deposit<T, M, T0, T1, T2, NT>;
+        kern = k_deposit<T, M, T0, T1, T2, NT, BLR>;
     }
     // the attribute is per device and only needs raising: remember the largest value set
     constexpr int kMaxDev = 64;
@@ -1247,6 +1350,56 @@ cudaError_t launch_deposit_m(const AssignPlan &pl, const uint32_t *offsets, cons
         else return launch_deposit_t<float, M, 16, 16, 16, 256>(pl, offsets, q, rf, grids, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+// The direct truncated-BL deposit (gather tiles 16^3 / 8^3 in FP32, 8x8x16 / 8^3 in FP64).
+template <int R>
+cudaError_t launch_deposit_bl(const AssignPlan &pl, const uint32_t *offsets, const unsigned *q, const void *rec,
+                              void *grids, cudaStream_t s)
+{
+    constexpr int M = 2 * R;
+    const auto *rf = static_cast<const Record<float> *>(rec);
+    const auto *rd = static_cast<const Record<double> *>(rec);
+    switch (pl.tile) {
+    case 0: return launch_deposit_t<float, M, 16, 16, 16, 256, R>(pl, offsets, q, rf, grids, s);
+    case 3: return launch_deposit_t<float, M, 8, 8, 8, 128, R>(pl, offsets, q, rf, grids, s);
+    case 4: return launch_deposit_t<double, M, 8, 8, 16, 256, R>(pl, offsets, q, rd, grids, s);
+    case 6: return launch_deposit_t<double, M, 8, 8, 8, 128, R>(pl, offsets, q, rd, grids, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// c_n = (1/2 pi) int Sigma_4(w)^{-1/2} e^{i n w} dw by the periodic trapezoid rule on 4096
+// points (spectrally accurate for this smooth periodic integrand), with
+// Sigma_4(w) = (2416 + 2382 cos w + 240 cos 2w + 2 cos 3w) / 5040 from the integer samples
+// of the order-8 B-spline; copied to constant memory once per device.
+cudaError_t set_bl_coefficients()
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    constexpr int N = 4096;
+    constexpr double kPi = 3.14159265358979323846;
+    double c[8] = {};
+    for (int k = 0; k < N; ++k) {
+        const double w = 2.0 * kPi * k / N;
+        const double sig = (2416.0 + 2382.0 * std::cos(w) + 240.0 * std::cos(2 * w) + 2.0 * std::cos(3 * w)) / 5040.0;
+        const double f = 1.0 / std::sqrt(sig);
+        for (int n = 0; n < 8; ++n) c[n] += f * std::cos(n * w);
+    }
+    float cf[8];
+    for (int n = 0; n < 8; ++n) {
+        c[n] /= N;
+        cf[n] = static_cast<float>(c[n]);
+    }
+    if ((e = cudaMemcpyToSymbol(c_bl_f, cf, sizeof cf)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_bl_d, c, sizeof c)) != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) done[dev] = true;
+    return cudaSuccess;
 }
 
 template <typename T>
@@ -1362,6 +1515,17 @@ cudaError_t launch_deposit(const AssignPlan &pl, void *scratch, void *grids, cud
     const void *rec = sc + pl.off_records;
     float *halo = pl.off_halo ? reinterpret_cast<float *>(sc + pl.off_halo) : nullptr;
     cudaError_t e;
+    if (pl.bl_radius > 0) {
+        if ((e = set_bl_coefficients()) != cudaSuccess) return e;
+        switch (pl.bl_radius) {
+        case 2: e = launch_deposit_bl<2>(pl, offsets, qmax, rec, grids, s); break;
+        case 3: e = launch_deposit_bl<3>(pl, offsets, qmax, rec, grids, s); break;
+        case 4: e = launch_deposit_bl<4>(pl, offsets, qmax, rec, grids, s); break;
+        default: return cudaErrorInvalidValue;
+        }
+        st.launches++;
+        return e;
+    }
     switch (pl.order) {
     case 1: e = launch_deposit_m<1>(pl, offsets, qmax, rec, grids, halo, s); break;
     case 2: e = launch_deposit_m<2>(pl, offsets, qmax, rec, grids, halo, s); break;

@@ -95,6 +95,8 @@ pkmom_status check_params(pkmom_ctx *ctx, const pkmom_params *p)
     if (!(hi <= 0.5 * p->ng) || !(lo < hi)) return fail(ctx, PKMOM_EINVAL, "need 0 < kmin_kf < kmax_kf <= ng/2");
     if (p->theta_sn_mode != 0 && p->theta_sn_mode != 1) return fail(ctx, PKMOM_EINVAL, "theta_sn_mode must be 0 or 1");
     if (!std::isfinite(p->theta_scale)) return fail(ctx, PKMOM_EINVAL, "theta_scale must be finite");
+    if (p->bl_radius != 0 && (p->bl_radius < 2 || p->bl_radius > 4 || p->order != 4))
+        return fail(ctx, PKMOM_EINVAL, "bl_radius must be 0, or 2..4 with order 4");
     return PKMOM_OK;
 }
 
@@ -114,6 +116,7 @@ AssignPlan plan_assign(const pkmom_params &p, int64_t n, int num_sms, int tile_o
     AssignPlan pl;
     pl.ng = p.ng;
     pl.order = p.order;
+    pl.bl_radius = p.bl_radius;
     pl.prec = p.precision;
     const double cells = double(p.ng) * p.ng * p.ng;
     // deposit tile: the largest listed shape that divides ng, for this precision
@@ -132,11 +135,17 @@ AssignPlan plan_assign(const pkmom_params &p, int64_t n, int num_sms, int tile_o
     // cubic order at half a particle per cell or more: home tiles (each particle deposited
     // once, by the tile owning its cell)
     const double ppc = double(n) / cells;
-    if (p.precision == PKMOM_F32 && p.order == 4 && p.ng % 16 == 0 && ppc >= 0.5) pl.tile = kHomeTile;
+    if (p.precision == PKMOM_F32 && p.order == 4 && p.bl_radius == 0 && p.ng % 16 == 0 && ppc >= 0.5)
+        pl.tile = kHomeTile;
     if (tile_override >= 0) {
         int d[3];
         deposit_tile_shape(tile_override, p.precision, d);
         if (d[0] && p.ng % d[0] == 0 && p.ng % d[1] == 0 && p.ng % d[2] == 0) pl.tile = tile_override;
+    }
+    // the direct BL deposit is built for the gather tiles 16^3 / 8^3 (FP32) and 8x8x16 / 8^3 (FP64)
+    if (p.bl_radius != 0) {
+        const bool big = p.ng % 16 == 0;
+        pl.tile = p.precision == PKMOM_F32 ? (big ? 0 : 3) : (big ? 4 : 6);
     }
     int td[3];
     deposit_tile_shape(pl.tile, p.precision, td);
@@ -258,13 +267,15 @@ pkmom_status get_tables(pkmom_ctx *ctx, const pkmom_params &p, cudaStream_t s, c
 {
     const double lo = umin_of(p), hi = umax_of(p);
     for (auto &t : ctx->tables)
-        if (t.ng == p.ng && t.order == p.order && t.nbins == p.nbins && t.umin == lo && t.umax == hi &&
+        if (t.ng == p.ng && t.order == p.order && t.direct == (p.bl_radius != 0) && t.nbins == p.nbins &&
+            t.umin == lo && t.umax == hi &&
             t.prec == p.precision) {
             *out = &t;
             return PKMOM_OK;
         }
     SpectraTables t;
-    cudaError_t e = build_spectra_tables(t, p.ng, p.order, p.nbins, lo, hi, p.precision, ctx->num_sms, s, ctx->st);
+    cudaError_t e = build_spectra_tables(t, p.ng, p.order, p.bl_radius != 0, p.nbins, lo, hi, p.precision,
+                                         ctx->num_sms, s, ctx->st);
     if (e != cudaSuccess) {
         free_spectra_tables(t);
         return cuda_fail(ctx, e, "building spectra tables");

@@ -28,6 +28,7 @@ template <typename T> struct Record { Vec4<T> u; Vec4<T> q; };
 // Host-side decisions for one assignment (see plan_assign in capi.cu).
 struct AssignPlan {
     int ng = 0, order = 4, prec = PKMOM_F32;
+    int bl_radius = 0;       // > 0: direct truncated BL deposit of this radius (cells)
     int sshift = 0;          // z-segment length S = 1 << sshift cells per sort key
     int64_t nkeys = 0;       // ng * ng * (ng >> sshift)
     int tile = 0;            // deposit tile id (see deposit launcher)
@@ -65,6 +66,7 @@ void deposit_tile_shape(int tile, int prec, int dims[3]);
 // ---------------------------------------------------------------- spectra.cu
 struct SpectraTables {
     int ng = 0, order = 0, nbins = 0, prec = -1;
+    bool direct = false;         // grids assigned with the BL function itself (no Fourier factor)
     double umin = 0, umax = 0;
     int nsq_max = 0;
     uint16_t *bintab = nullptr;  // [nsq_max + 1] shell of |n|^2, 0xFFFF outside
@@ -79,8 +81,8 @@ struct SpectraTables {
     double *item_partials = nullptr;  // [ng * nbins][kBinVals] (shell-major binning)
     int shell_blocks = 0;
 };
-cudaError_t build_spectra_tables(SpectraTables &t, int ng, int order, int nbins, double umin, double umax, int prec,
-                                 int num_sms, cudaStream_t s, LaunchStats &st);
+cudaError_t build_spectra_tables(SpectraTables &t, int ng, int order, bool direct, int nbins, double umin,
+                                 double umax, int prec, int num_sms, cudaStream_t s, LaunchStats &st);
 void free_spectra_tables(SpectraTables &t);
 cudaError_t launch_bin(const SpectraTables &t, const void *grids, const double *moments_dev, cudaStream_t s,
                        LaunchStats &st);

@@ -517,11 +517,12 @@ void free_spectra_tables(SpectraTables &t)
     t = SpectraTables{};
 }
 
-cudaError_t build_spectra_tables(SpectraTables &t, int ng, int order, int nbins, double umin, double umax, int prec,
-                                 int num_sms, cudaStream_t s, LaunchStats &st)
+cudaError_t build_spectra_tables(SpectraTables &t, int ng, int order, bool direct, int nbins, double umin,
+                                 double umax, int prec, int num_sms, cudaStream_t s, LaunchStats &st)
 {
     t.ng = ng;
     t.order = order;
+    t.direct = direct;
     t.nbins = nbins;
     t.umin = umin;
     t.umax = umax;
@@ -541,13 +542,16 @@ cudaError_t build_spectra_tables(SpectraTables &t, int ng, int order, int nbins,
     for (int i = 0; i < ng; ++i) {
         const int ni = i < ng / 2 ? i : i - ng;
         const double w = kTwoPi * ni / ng;
-        gfd[i] = 1.0 / bhat2(w, order);
         hfd[i] = sigma_m(w, order) / bhat2(w, order);
+        // B-spline grids carry the BL field times prod Sigma^{-1/2}: 1/W^2 of the BL field
+        // is then 1/Bhat^2 per axis; grids assigned with the BL function itself take
+        // 1/W^2 = Sigma/Bhat^2
+        gfd[i] = direct ? hfd[i] : 1.0 / bhat2(w, order);
     }
     for (int i = 0; i < nh; ++i) {
         const double w = kTwoPi * i / ng;
-        ghd[i] = 1.0 / bhat2(w, order);
         hhd[i] = sigma_m(w, order) / bhat2(w, order);
+        ghd[i] = direct ? hhd[i] : 1.0 / bhat2(w, order);
     }
     // shell b is the interval thresh[b] <= |n|^2 < thresh[b + 1] (bins are monotone in |n|^2)
     std::vector<int> thresh(nbins + 1, t.nsq_max + 1);
@@ -713,7 +717,7 @@ __device__ const double kEF4[4] = {151.0 / 315.0, 397.0 / 1680.0, 1.0 / 42.0, 1.
 // the same expressions as build_spectra_tables (correctly rounded sqrt and division,
 // so the shell of every |n|^2 is the same).
 template <typename T>
-__global__ void k_static_tables(int ng, int order, int nbins, double umin, double umax, int nsq_max,
+__global__ void k_static_tables(int ng, int order, bool direct, int nbins, double umin, double umax, int nsq_max,
                                 uint16_t *__restrict__ bintab, T *__restrict__ gf, T *__restrict__ gh,
                                 double *__restrict__ hf, double *__restrict__ hh)
 {
@@ -745,10 +749,10 @@ __global__ void k_static_tables(int ng, int order, int nbins, double umin, doubl
         for (int k = 0; k < order; ++k) b2 *= sx;
         b2 *= b2;
         if (full) {
-            gf[j] = static_cast<T>(1.0 / b2);
+            gf[j] = static_cast<T>(direct ? s / b2 : 1.0 / b2);
             hf[j] = s / b2;
         } else {
-            gh[j] = static_cast<T>(1.0 / b2);
+            gh[j] = static_cast<T>(direct ? s / b2 : 1.0 / b2);
             hh[j] = s / b2;
         }
     }
@@ -813,7 +817,7 @@ extern "C" pkmom_status pkmom_spectra_static(const pkmom_params *p, const void *
     if (!p || !grids || !moments_dev || !out_dev) return PKMOM_EINVAL;
     if (!(p->box_L > 0) || p->ng < 16 || p->ng > 1024 || p->ng % 8 || p->order < 1 || p->order > 4 ||
         (p->precision != PKMOM_F32 && p->precision != PKMOM_F64) || p->nbins < 1 || p->theta_sn_mode < 0 ||
-        p->theta_sn_mode > 1)
+        p->theta_sn_mode > 1 || (p->bl_radius != 0 && (p->bl_radius < 2 || p->bl_radius > 4 || p->order != 4)))
         return PKMOM_EINVAL;
     if (p->nbins > kStaticMaxBins) return PKMOM_EUNSUPPORTED;  // beyond the static scratch's shell limit
     const double umin = p->kmin_kf > 0 ? p->kmin_kf : 1.0;
@@ -831,6 +835,7 @@ extern "C" pkmom_status pkmom_spectra_static(const pkmom_params *p, const void *
     SpectraTables t;
     t.ng = ng;
     t.order = p->order;
+    t.direct = p->bl_radius != 0;
     t.nbins = nbins;
     t.prec = p->precision;
     t.umin = umin;
@@ -847,11 +852,11 @@ extern "C" pkmom_status pkmom_spectra_static(const pkmom_params *p, const void *
 
     const int tb = 256, tg = (nsq_max + 1 + tb - 1) / tb < 256 ? (nsq_max + 1 + tb - 1) / tb : 256;
     if (p->precision == PKMOM_F32)
-        k_static_tables<float><<<tg, tb, 0, s>>>(ng, p->order, nbins, umin, umax, nsq_max, t.bintab,
+        k_static_tables<float><<<tg, tb, 0, s>>>(ng, p->order, p->bl_radius != 0, nbins, umin, umax, nsq_max, t.bintab,
                                                  static_cast<float *>(t.g_full), static_cast<float *>(t.g_half),
                                                  t.h_full, t.h_half);
     else
-        k_static_tables<double><<<tg, tb, 0, s>>>(ng, p->order, nbins, umin, umax, nsq_max, t.bintab,
+        k_static_tables<double><<<tg, tb, 0, s>>>(ng, p->order, p->bl_radius != 0, nbins, umin, umax, nsq_max, t.bintab,
                                                   static_cast<double *>(t.g_full), static_cast<double *>(t.g_half),
                                                   t.h_full, t.h_half);
     const uint32_t nmodes = static_cast<uint32_t>(static_cast<int64_t>(ng) * ng * nh);

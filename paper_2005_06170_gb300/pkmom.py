@@ -34,7 +34,8 @@ class Params(ctypes.Structure):
     _fields_ = [("box_L", ctypes.c_double), ("ng", ctypes.c_int), ("order", ctypes.c_int),
                 ("precision", ctypes.c_int), ("nbins", ctypes.c_int), ("kmin_kf", ctypes.c_double),
                 ("kmax_kf", ctypes.c_double), ("theta_scale", ctypes.c_double),
-                ("subtract_shot_noise", ctypes.c_int), ("bulk", ctypes.c_int), ("theta_sn_mode", ctypes.c_int)]
+                ("subtract_shot_noise", ctypes.c_int), ("bulk", ctypes.c_int), ("theta_sn_mode", ctypes.c_int),
+                ("bl_radius", ctypes.c_int)]
 
 
 class Catalog(ctypes.Structure):
@@ -99,7 +100,8 @@ EXPORTED = ("pkmom_params_default", "pkmom_create", "pkmom_destroy", "pkmom_stre
 
 def params(box_L: float, ng: int, nbins: int, *, order: int = 4, precision: int = F32, kmin_kf: float = 1.0,
            kmax_kf: float | None = None, theta_scale: float = 1.0, subtract_shot_noise: bool = True,
-           bulk: bool = True, theta_sn: str = "tensor") -> Params:
+           bulk: bool = True, theta_sn: str = "tensor", bl_radius: int = 0) -> Params:
+    """bl_radius > 0: the BL function truncated to that many cells, deposited directly."""
     p = Params()
     lib().pkmom_params_default(ctypes.byref(p), float(box_L), int(ng), int(nbins))
     p.order = order
@@ -110,6 +112,7 @@ def params(box_L: float, ng: int, nbins: int, *, order: int = 4, precision: int 
     p.subtract_shot_noise = int(bool(subtract_shot_noise))
     p.bulk = int(bool(bulk))
     p.theta_sn_mode = {"tensor": 0, "isotropic": 1}[theta_sn]
+    p.bl_radius = int(bl_radius)
     return p
 
 
