@@ -85,6 +85,29 @@ enum {
     PKMOM_NROWS = 14
 };
 
+/* Rows of the (|k|, mu)-binned output of pkmom_spectra_mu: out[row * ncells + cell],
+ * cell = bin * nmu + mu_bin. Spectra with their shot noise removed; Re/Im of the complex
+ * density x momentum-divergence cross spectrum in the paper's convention. */
+enum {
+    PKMOM_MU_ROW_K = 0,       /* mode-weighted mean |k| */
+    PKMOM_MU_ROW_MU = 1,      /* mode-weighted mean mu */
+    PKMOM_MU_ROW_NMODES = 2,  /* number of modes (full sphere, Nyquist modes left out) */
+    PKMOM_MU_ROW_PDD = 3,
+    PKMOM_MU_ROW_PPP = 4,
+    PKMOM_MU_ROW_PTT = 5,     /* the theta shot noise k.Q.k depends on mu_b (Eq. thetanoise) */
+    PKMOM_MU_ROW_RE_DT = 6,
+    PKMOM_MU_ROW_IM_DT = 7,   /* -k mu_b (v_b/Haf) P with a bulk flow (Eq. bfpdpx) */
+    PKMOM_MU_ROW_PPP_B = 8,   /* bulk flow removed (Sec. 3.1) */
+    PKMOM_MU_ROW_PTT_B = 9,
+    PKMOM_MU_ROW_RE_DT_B = 10,
+    PKMOM_MU_ROW_IM_DT_B = 11,
+    PKMOM_MU_ROW_RE_DPB_B = 12, /* Re P_delta p'_b, p'_b = p'.v_b/|v_b| (Eq. bfpp) */
+    PKMOM_MU_ROW_SNDD = 13,   /* subtracted shot noise of P_dd */
+    PKMOM_MU_ROW_SNTT = 14,   /* subtracted shot noise of P_theta */
+    PKMOM_MU_ROW_IM_SNDT = 15,/* subtracted (imaginary) shot noise of P_delta-theta (Eq. rawPx) */
+    PKMOM_MU_NROWS = 16
+};
+
 /* A particle catalogue. x,y,z,vx,vy,vz are element pointers with a common stride
  * in elements (1 for separate arrays, 3 for interleaved (n,3) position and
  * velocity arrays). mass may be NULL (unit masses). dtype is PKMOM_F32 or
@@ -164,6 +187,20 @@ pkmom_status pkmom_fft(pkmom_ctx *ctx, const pkmom_params *p, void *grids, void 
  * the per-shell mode tables (allocates; call once before any stream capture). */
 pkmom_status pkmom_spectra(pkmom_ctx *ctx, const pkmom_params *p, const void *grids,
                            const void *moments_dev, double *out_dev, void *stream);
+
+/* Step 4 in bins of |k| (the shells of p) and of mu = k.e/(|k| |e|), nmu linear bins on
+ * [-1, 1]: the direction-dependent parts that shell averages cancel, the imaginary
+ * cross spectrum -i k mu_b (v_b/Haf) P of a bulk flow and the mu_b-dependent shot noise
+ * of theta (Sec. 2.2 Eq. thetanoise, Sec. 3.2 Eq. bfpdpx, Fig. bfPpdiff). direction: 3
+ * host doubles (any length > 0), or NULL for the catalogue's bulk flow. Each mode is
+ * counted once over the full sphere; modes with a Nyquist component (no direction
+ * sign) are left out. The mu bin is decided in FP32: m = floor((mu + 1) nmu/2) with
+ * mu = ((n0 e0 + n1 e1) + n2 e2) / sqrt(|n|^2), e normalised in FP64 and rounded to
+ * FP32. out_dev: device, PKMOM_MU_NROWS * nbins * nmu doubles; empty cells give NaN.
+ * nmu in 1..64 (PKMOM_EINVAL otherwise). Allocates context-owned work arrays on first
+ * use (and when larger ones are needed). */
+pkmom_status pkmom_spectra_mu(pkmom_ctx *ctx, const pkmom_params *p, const void *grids, const void *moments_dev,
+                              const double *direction, int nmu, double *out_dev, void *stream);
 
 /* Steps 1-4 on a device catalogue, with grids and scratch owned by the context
  * (allocated on first use and grown when needed). out_dev as for pkmom_spectra. */

@@ -43,6 +43,11 @@ struct pkmom_ctx {
     size_t out_bytes = 0;
     void *staging = nullptr;
     size_t staging_bytes = 0;
+    // work arrays of pkmom_spectra_mu
+    void *mu_partials = nullptr;
+    size_t mu_partials_bytes = 0;
+    void *mu_sums = nullptr;
+    size_t mu_sums_bytes = 0;
     // tuning overrides (-1: automatic)
     int tune_tile = -1;
     int tune_list_cap = -1;
@@ -373,6 +378,8 @@ pkmom_status pkmom_destroy(pkmom_ctx *ctx)
     cudaFree(ctx->moments);
     cudaFree(ctx->out_dev);
     cudaFree(ctx->staging);
+    cudaFree(ctx->mu_partials);
+    cudaFree(ctx->mu_sums);
     cudaFree(ctx->d_err);
     delete ctx;
     return PKMOM_OK;
@@ -482,6 +489,39 @@ pkmom_status pkmom_spectra(pkmom_ctx *ctx, const pkmom_params *p, const void *gr
         PK_CUDA(launch_finalize(*t, *p, static_cast<const double *>(moments_dev), out_dev, st, ctx->st, true),
                 "finalize");
     }
+    return PKMOM_OK;
+}
+
+pkmom_status pkmom_spectra_mu(pkmom_ctx *ctx, const pkmom_params *p, const void *grids, const void *moments_dev,
+                              const double *direction, int nmu, double *out_dev, void *stream)
+{
+    if (!ctx) return PKMOM_EINVAL;
+    pkmom_status s;
+    if ((s = check_params(ctx, p)) != PKMOM_OK) return s;
+    if (!grids || !moments_dev || !out_dev) return fail(ctx, PKMOM_EINVAL, "null grids, moments or output");
+    if (nmu < 1 || nmu > 64) return fail(ctx, PKMOM_EINVAL, "nmu must be 1..64");
+    double dir[3];
+    if (direction) {
+        const double nrm = std::sqrt(direction[0] * direction[0] + direction[1] * direction[1] +
+                                     direction[2] * direction[2]);
+        if (!(nrm > 0) || !std::isfinite(nrm)) return fail(ctx, PKMOM_EINVAL, "direction must be finite and non-zero");
+        for (int a = 0; a < 3; ++a) dir[a] = direction[a] / nrm;
+    }
+    PK_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t st = as_stream(stream);
+    const SpectraTables *t = nullptr;
+    if ((s = get_tables(ctx, *p, st, &t)) != PKMOM_OK) return s;
+    if ((s = ensure(ctx, &ctx->mu_partials, &ctx->mu_partials_bytes, spectra_mu_partial_bytes(p->ng, p->nbins, nmu),
+                    "mu partials")) != PKMOM_OK)
+        return s;
+    if ((s = ensure(ctx, &ctx->mu_sums, &ctx->mu_sums_bytes, spectra_mu_sum_bytes(p->nbins, nmu), "mu sums")) !=
+        PKMOM_OK)
+        return s;
+    StageTimer tm(ctx, PKMOM_STAGE_BIN, st);
+    PK_CUDA(launch_spectra_mu(*t, *p, grids, static_cast<const double *>(moments_dev), direction ? dir : nullptr, nmu,
+                              static_cast<double *>(ctx->mu_partials), static_cast<double *>(ctx->mu_sums), out_dev,
+                              st, ctx->st),
+            "mu binning");
     return PKMOM_OK;
 }
 

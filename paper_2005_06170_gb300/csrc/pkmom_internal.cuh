@@ -93,4 +93,11 @@ cudaError_t launch_bin_shells(const SpectraTables &t, const void *grids, const d
 cudaError_t launch_finalize(const SpectraTables &t, const pkmom_params &p, const double *moments_dev,
                             double *out, cudaStream_t s, LaunchStats &st, bool sums_ready);
 
+// (|k|, mu)-binned spectra: per-item partials (ng * nbins * nmu items) and cell sums
+cudaError_t launch_spectra_mu(const SpectraTables &t, const pkmom_params &p, const void *grids,
+                              const double *moments_dev, const double *dir, int nmu, double *partials, double *sums,
+                              double *out, cudaStream_t s, LaunchStats &st);
+size_t spectra_mu_partial_bytes(int ng, int nbins, int nmu);
+size_t spectra_mu_sum_bytes(int nbins, int nmu);
+
 }  // namespace pkmom

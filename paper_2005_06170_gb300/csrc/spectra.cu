@@ -875,3 +875,281 @@ extern "C" pkmom_status pkmom_spectra_static(const pkmom_params *p, const void *
         return PKMOM_ECUDA;
     return PKMOM_OK;
 }
+
+// ---------------------------------------------------------------- spectra in (|k|, mu) bins
+// Shells of |k| split into nmu linear bins of mu = n.e / |n| in [-1, 1] (e: a given
+// direction, or the bulk flow), for the direction-dependent parts of Sec. 2.2 (Eq.
+// thetanoise) and Sec. 3.2 (Eq. bfpdpx): the imaginary density x momentum-divergence
+// cross spectrum -i k mu_b (v_b/Haf) P and the mu_b-dependent shot noise, which shell
+// averages cancel. A stored half-spectrum mode n with 0 < n_z < ng/2 stands for n and -n:
+// it is added at mu(n) and, mirrored (odd terms negated), at mu(-n) = -mu(n). Modes with
+// a Nyquist component have no direction sign and are left out. The mu bin is decided in
+// FP32 with correctly rounded operations in a fixed order:
+// m = floor(((n0 e0 + n1 e1) + n2 e2) / sqrt(|n|^2) + 1) * nmu/2), clipped.
+namespace pkmom {
+namespace {
+
+// Per-item sums (each times the mode weight; data values also times g = 1/W^2):
+//  0 |F_d|^2  1 |F_p|^2  2 |F_p'|^2  3 |n.F_p|^2  4 |n.F_p'|^2
+//  5 Im z  6 Re z  (z = conj(F_d) n.F_p)   7 Im z'  8 Re z'  (F_p')   9 Re conj(F_d) e_b.F_p'
+//  10 count  11 |n|  12 mu  13 h  14-19 h n_a n_b (xx yy zz xy xz yz)  20-22 h n_a
+constexpr int kMuVals = 23;
+__device__ __forceinline__ bool mu_odd(int k) { return k == 6 || k == 8 || k == 12 || k >= 20; }
+
+__device__ __forceinline__ int mu_bin(float n0, float n1, float n2, float e0, float e1, float e2, float r, int nmu)
+{
+    const float d = __fadd_rn(__fadd_rn(__fmul_rn(n0, e0), __fmul_rn(n1, e1)), __fmul_rn(n2, e2));
+    const float mu = __fdiv_rn(d, r);
+    const int m = static_cast<int>(floorf(__fmul_rn(__fadd_rn(mu, 1.0f), 0.5f * static_cast<float>(nmu))));
+    return m < 0 ? 0 : (m >= nmu ? nmu - 1 : m);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBinThreads, 2)
+k_bin_mu(const Cx<T> *__restrict__ F, int64_t gstride, int ng, int nbins, int nmu, const int *__restrict__ thresh,
+         const T *__restrict__ gf, const T *__restrict__ gh, const double *__restrict__ hf,
+         const double *__restrict__ hh, const double *__restrict__ mom, double ge0, double ge1, double ge2,
+         int bulk_dir, double *__restrict__ partials)
+{
+    constexpr int NW = kBinThreads / 32;
+    __shared__ int s_lo[NW][32], s_pre[NW][32], s_n1[NW][32];
+    __shared__ int64_t s_row[NW][32];
+    __shared__ T s_g[NW][32];
+    __shared__ T s_h[NW][32];
+    const int nh = ng / 2 + 1;
+    const double Mtot = mom[0];
+    const double vbd[3] = {mom[2] / Mtot, mom[3] / Mtot, mom[4] / Mtot};
+    const double vbn = sqrt(vbd[0] * vbd[0] + vbd[1] * vbd[1] + vbd[2] * vbd[2]);
+    const T vb0 = static_cast<T>(vbd[0]), vb1 = static_cast<T>(vbd[1]), vb2 = static_cast<T>(vbd[2]);
+    const T eb0 = vbn > 0 ? static_cast<T>(vbd[0] / vbn) : T(0), eb1 = vbn > 0 ? static_cast<T>(vbd[1] / vbn) : T(0),
+            eb2 = vbn > 0 ? static_cast<T>(vbd[2] / vbn) : T(0);
+    double ed0 = ge0, ed1 = ge1, ed2 = ge2;  // unit direction in FP64
+    if (bulk_dir) {
+        ed0 = vbn > 0 ? vbd[0] / vbn : 0.0;
+        ed1 = vbn > 0 ? vbd[1] / vbn : 0.0;
+        ed2 = vbn > 0 ? vbd[2] / vbn : 0.0;
+    }
+    // the bin decision in FP32; the mean mu in the grid precision
+    const float e0 = static_cast<float>(ed0), e1 = static_cast<float>(ed1), e2 = static_cast<float>(ed2);
+    const T et0 = static_cast<T>(ed0), et1 = static_cast<T>(ed1), et2 = static_cast<T>(ed2);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nwarps = gridDim.x * NW;
+    const int nitems = ng * nbins * nmu;
+    for (int item = blockIdx.x * NW + w; item < nitems; item += nwarps) {
+        const int m = item % nmu;
+        const int b = (item / nmu) % nbins;
+        const int i0 = item / (nmu * nbins);
+        const int n0 = i0 < ng / 2 ? i0 : i0 - ng;
+        const int lo2 = thresh[b], hi2 = thresh[b + 1];  // lo2 <= |n|^2 < hi2
+        T s[kMuVals], c[kMuVals];
+#pragma unroll
+        for (int k = 0; k < kMuVals; ++k) s[k] = T(0), c[k] = T(0);
+        const int rem = hi2 - 1 - n0 * n0;
+        if (i0 != ng / 2 && hi2 > lo2 && rem >= 0) {
+            const int R1 = isqrt_floor(rem);
+            const int n1lo = max(1 - ng / 2, -R1), n1hi = min(ng / 2 - 1, R1);
+            const T g0 = gf[i0];
+            const double h0 = hf[i0];
+            for (int r0 = n1lo; r0 <= n1hi; r0 += 32) {
+                const int n1 = r0 + lane;
+                const bool row = n1 <= n1hi;
+                int l_lo = 0, len = 0;
+                if (row) {
+                    const int r2 = n0 * n0 + n1 * n1;
+                    const int top = hi2 - 1 - r2;
+                    if (top >= 0) {
+                        const int lh = min(isqrt_floor(top), nh - 2);  // no Nyquist plane
+                        const int need = lo2 - r2;
+                        const int ll = need <= 0 ? 0 : isqrt_floor(need - 1) + 1;
+                        if (lh >= ll) l_lo = ll, len = lh - ll + 1;
+                    }
+                }
+                int inc = len;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, inc, d);
+                    if (lane >= d) inc += t;
+                }
+                const int total = __shfl_sync(0xffffffffu, inc, 31);
+                if (total == 0) continue;
+                const int i1 = row ? (n1 < 0 ? n1 + ng : n1) : 0;
+                s_lo[w][lane] = l_lo;
+                s_pre[w][lane] = inc - len;
+                s_n1[w][lane] = n1;
+                s_row[w][lane] = (static_cast<int64_t>(i0) * ng + i1) * nh;
+                s_g[w][lane] = row ? g0 * gf[i1] : T(0);
+                s_h[w][lane] = row ? static_cast<T>(h0 * hf[i1]) : T(0);
+                __syncwarp();
+                for (int mm = lane; mm < total; mm += 32) {
+                    int j = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1)
+                        if (s_pre[w][j + step] <= mm) j += step;
+                    const int l = s_lo[w][j] + (mm - s_pre[w][j]);
+                    const int nn1 = s_n1[w][j];
+                    const int nsq = n0 * n0 + nn1 * nn1 + l * l;
+                    const float rn = __fsqrt_rn(static_cast<float>(nsq));
+                    const float fn0 = static_cast<float>(n0), fn1 = static_cast<float>(nn1), fl = static_cast<float>(l);
+                    const bool fwd = mu_bin(fn0, fn1, fl, e0, e1, e2, rn, nmu) == m;
+                    const bool mir = l > 0 && mu_bin(-fn0, -fn1, -fl, e0, e1, e2, rn, nmu) == m;
+                    if (!fwd && !mir) continue;
+                    const int64_t mi = s_row[w][j] + l;
+                    const T g = s_g[w][j] * gh[l];
+                    const T th = s_h[w][j] * static_cast<T>(hh[l]);
+                    const Cx<T> dd = F[mi], p0 = F[gstride + mi], p1 = F[2 * gstride + mi], p2 = F[3 * gstride + mi];
+                    const T a0 = static_cast<T>(n0), a1 = static_cast<T>(nn1), a2 = static_cast<T>(l);
+                    const T kr = a0 * p0.x + a1 * p1.x + a2 * p2.x, ki = a0 * p0.y + a1 * p1.y + a2 * p2.y;
+                    const Cx<T> q0{p0.x - vb0 * dd.x, p0.y - vb0 * dd.y};
+                    const Cx<T> q1{p1.x - vb1 * dd.x, p1.y - vb1 * dd.y};
+                    const Cx<T> q2{p2.x - vb2 * dd.x, p2.y - vb2 * dd.y};
+                    const T jr = a0 * q0.x + a1 * q1.x + a2 * q2.x, ji = a0 * q0.y + a1 * q1.y + a2 * q2.y;
+                    const T br = eb0 * q0.x + eb1 * q1.x + eb2 * q2.x, bi = eb0 * q0.y + eb1 * q1.y + eb2 * q2.y;
+                    T v[kMuVals];
+                    v[0] = g * (dd.x * dd.x + dd.y * dd.y);
+                    v[1] = g * (p0.x * p0.x + p0.y * p0.y + p1.x * p1.x + p1.y * p1.y + p2.x * p2.x + p2.y * p2.y);
+                    v[2] = g * (q0.x * q0.x + q0.y * q0.y + q1.x * q1.x + q1.y * q1.y + q2.x * q2.x + q2.y * q2.y);
+                    v[3] = g * (kr * kr + ki * ki);
+                    v[4] = g * (jr * jr + ji * ji);
+                    v[5] = g * (dd.x * ki - dd.y * kr);  // Im(conj(F_d) n.F_p)
+                    v[6] = g * (dd.x * kr + dd.y * ki);  // Re(conj(F_d) n.F_p)
+                    v[7] = g * (dd.x * ji - dd.y * jr);
+                    v[8] = g * (dd.x * jr + dd.y * ji);
+                    v[9] = g * (dd.x * br + dd.y * bi);
+                    const T rt = sqrt(static_cast<T>(nsq));
+                    v[10] = T(1);
+                    v[11] = rt;
+                    v[12] = (a0 * et0 + a1 * et1 + a2 * et2) / rt;
+                    v[13] = th;
+                    v[14] = th * a0 * a0;
+                    v[15] = th * a1 * a1;
+                    v[16] = th * a2 * a2;
+                    v[17] = th * a0 * a1;
+                    v[18] = th * a0 * a2;
+                    v[19] = th * a1 * a2;
+                    v[20] = th * a0;
+                    v[21] = th * a1;
+                    v[22] = th * a2;
+#pragma unroll
+                    for (int k = 0; k < kMuVals; ++k) {
+                        // forward and mirrored contributions (the mirror negates odd terms)
+                        const T x = (fwd ? v[k] : T(0)) + (mir ? (mu_odd(k) ? -v[k] : v[k]) : T(0));
+                        const T y = x - c[k];
+                        const T t = s[k] + y;
+                        c[k] = (t - s[k]) - y;
+                        s[k] = t;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kMuVals; ++k) {
+            const double dsum = warp_sum_pair(s[k], -c[k]);
+            if (lane == 0) partials[static_cast<int64_t>(item) * kMuVals + k] = dsum;
+        }
+    }
+}
+
+struct MuParams {
+    double V, kf, ts;
+    int ncells;
+};
+
+// One thread per (shell, mu) cell: the sums of k_bin_mu -> spectra with the shot noise
+// subtracted in FP64 (the same algebra as k_finalize, with the odd terms kept).
+__global__ void k_finalize_mu(const double *__restrict__ sums /*[kMuVals][ncells]*/, const double *__restrict__ mom,
+                              MuParams fp, double *__restrict__ out /*[PKMOM_MU_NROWS][ncells]*/)
+{
+    const int cidx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nc = fp.ncells;
+    if (cidx >= nc) return;
+    auto S = [&](int k) { return sums[k * nc + cidx]; };
+    auto put = [&](int row, double v) { out[row * nc + cidx] = v; };
+    const double n = S(10);
+    put(PKMOM_MU_ROW_NMODES, n);
+    if (!(n > 0.0)) {
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        for (int r = 0; r < PKMOM_MU_NROWS; ++r)
+            if (r != PKMOM_MU_ROW_NMODES) put(r, nan);
+        return;
+    }
+    const double M = mom[0], S2 = mom[1];
+    const double vb[3] = {mom[2] / M, mom[3] / M, mom[4] / M};
+    const double R[3] = {mom[5], mom[6], mom[7]};
+    const double *Q = mom + 8;
+    const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+    double Qb[6], Rb[3];
+    for (int k = 0; k < 6; ++k)
+        Qb[k] = Q[k] - vb[ia[k]] * R[ib[k]] - R[ia[k]] * vb[ib[k]] + vb[ia[k]] * vb[ib[k]] * S2;
+    for (int a = 0; a < 3; ++a) Rb[a] = R[a] - S2 * vb[a];
+    const double vbn = sqrt(vb[0] * vb[0] + vb[1] * vb[1] + vb[2] * vb[2]);
+    const double ebR = vbn > 0 ? (vb[0] * Rb[0] + vb[1] * Rb[1] + vb[2] * Rb[2]) / vbn : 0.0;
+    const double H = S(13);
+    double H2[6];
+    for (int k = 0; k < 6; ++k) H2[k] = S(14 + k);
+    const double H1[3] = {S(20), S(21), S(22)};
+    const double c = fp.V / (M * M * n);
+    const double ct = c * fp.ts * fp.ts * fp.kf * fp.kf, cx = c * fp.ts * fp.kf;
+    put(PKMOM_MU_ROW_K, fp.kf * S(11) / n);
+    put(PKMOM_MU_ROW_MU, S(12) / n);
+    const double sn_dd = c * S2 * H;
+    put(PKMOM_MU_ROW_PDD, c * S(0) - sn_dd);
+    put(PKMOM_MU_ROW_SNDD, sn_dd);
+    put(PKMOM_MU_ROW_PPP, c * (S(1) - (Q[0] + Q[1] + Q[2]) * H));
+    put(PKMOM_MU_ROW_PPP_B, c * (S(2) - (Qb[0] + Qb[1] + Qb[2]) * H));
+    const double sn_tt = ct * qdot(Q, H2);
+    put(PKMOM_MU_ROW_PTT, ct * S(3) - sn_tt);
+    put(PKMOM_MU_ROW_SNTT, sn_tt);
+    put(PKMOM_MU_ROW_PTT_B, ct * S(4) - ct * qdot(Qb, H2));
+    // X = -i ts conj(F_d) k.F_p: Re X = ts Im z, Im X = -ts Re z; its shot noise
+    // -i ts (k.R) h is imaginary (Eq. rawPx)
+    const double im_sn = -cx * (R[0] * H1[0] + R[1] * H1[1] + R[2] * H1[2]);
+    const double im_sn_b = -cx * (Rb[0] * H1[0] + Rb[1] * H1[1] + Rb[2] * H1[2]);
+    put(PKMOM_MU_ROW_RE_DT, cx * S(5));
+    put(PKMOM_MU_ROW_IM_DT, -cx * S(6) - im_sn);
+    put(PKMOM_MU_ROW_IM_SNDT, im_sn);
+    put(PKMOM_MU_ROW_RE_DT_B, cx * S(7));
+    put(PKMOM_MU_ROW_IM_DT_B, -cx * S(8) - im_sn_b);
+    put(PKMOM_MU_ROW_RE_DPB_B, c * (S(9) - ebR * H));
+}
+
+}  // namespace
+
+cudaError_t launch_spectra_mu(const SpectraTables &t, const pkmom_params &p, const void *grids,
+                              const double *moments_dev, const double *dir /* unit, or nullptr */, int nmu,
+                              double *partials, double *sums, double *out, cudaStream_t s, LaunchStats &st)
+{
+    const int ng = t.ng, nh = ng / 2 + 1;
+    const int64_t gstride = static_cast<int64_t>(ng) * ng * nh;
+    const unsigned blocks = static_cast<unsigned>(t.shell_blocks);
+    const double d0 = dir ? dir[0] : 0.0, d1 = dir ? dir[1] : 0.0, d2 = dir ? dir[2] : 0.0;
+    const int bulk_dir = dir ? 0 : 1;
+    if (t.prec == PKMOM_F32)
+        k_bin_mu<float><<<blocks, kBinThreads, 0, s>>>(
+            static_cast<const Cx<float> *>(grids), gstride, ng, t.nbins, nmu, t.thresh,
+            static_cast<const float *>(t.g_full), static_cast<const float *>(t.g_half), t.h_full, t.h_half,
+            moments_dev, d0, d1, d2, bulk_dir, partials);
+    else
+        k_bin_mu<double><<<blocks, kBinThreads, 0, s>>>(
+            static_cast<const Cx<double> *>(grids), gstride, ng, t.nbins, nmu, t.thresh,
+            static_cast<const double *>(t.g_full), static_cast<const double *>(t.g_half), t.h_full, t.h_half,
+            moments_dev, d0, d1, d2, bulk_dir, partials);
+    const int ncells = t.nbins * nmu;
+    k_reduce_items<kMuVals><<<ncells, 256, 0, s>>>(partials, ng, ncells, sums);
+    MuParams fp;
+    fp.V = p.box_L * p.box_L * p.box_L;
+    fp.kf = kTwoPi / p.box_L;
+    fp.ts = p.theta_scale;
+    fp.ncells = ncells;
+    k_finalize_mu<<<(ncells + 127) / 128, 128, 0, s>>>(sums, moments_dev, fp, out);
+    st.launches += 3;
+    return cudaGetLastError();
+}
+
+size_t spectra_mu_partial_bytes(int ng, int nbins, int nmu)
+{
+    return static_cast<size_t>(ng) * nbins * nmu * kMuVals * sizeof(double);
+}
+size_t spectra_mu_sum_bytes(int nbins, int nmu) { return static_cast<size_t>(nbins) * nmu * kMuVals * sizeof(double); }
+
+}  // namespace pkmom

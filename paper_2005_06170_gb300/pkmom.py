@@ -28,6 +28,10 @@ ROW = {"k": 0, "n_modes": 1, "P_dd": 2, "P_pp": 3, "P_tt": 4, "P_dt": 5, "P_pp_b
 STAGES = ("hist", "scan", "scatter", "deposit", "fft", "bin", "final")
 STATUS = {0: "PKMOM_OK", -1: "PKMOM_EINVAL", -2: "PKMOM_ENOMEM", -3: "PKMOM_ECUDA", -4: "PKMOM_ECUFFT",
           -5: "PKMOM_ETIMEOUT", -6: "PKMOM_EUNSUPPORTED", -7: "PKMOM_ESCRATCH", -8: "PKMOM_EDATA"}
+# rows of pkmom_spectra_mu (out[row * nbins * nmu + bin * nmu + mu_bin])
+MU_NROWS = 16
+MU_ROW = {"k": 0, "mu": 1, "n_modes": 2, "P_dd": 3, "P_pp": 4, "P_tt": 5, "Re_dt": 6, "Im_dt": 7, "P_pp_b": 8,
+          "P_tt_b": 9, "Re_dt_b": 10, "Im_dt_b": 11, "Re_dpb_b": 12, "SN_dd": 13, "SN_tt": 14, "Im_SN_dt": 15}
 
 
 class Params(ctypes.Structure):
@@ -80,6 +84,7 @@ def lib():
         "pkmom_timing_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
         "pkmom_kernel_launches": (i64, [vp]),
         "pkmom_spectra_static": (i32, [ctypes.POINTER(Params), vp, vp, vp, vp]),
+        "pkmom_spectra_mu": (i32, [vp, ctypes.POINTER(Params), vp, vp, ctypes.POINTER(ctypes.c_double), i32, vp, vp]),
         "pkmom_set_tuning": (i32, [vp, i32, i32]),
         "pkmom_assign_scratch_bytes_tuned": (ctypes.c_size_t, [vp, ctypes.POINTER(Params), i64]),
     }
@@ -95,7 +100,7 @@ EXPORTED = ("pkmom_params_default", "pkmom_create", "pkmom_destroy", "pkmom_stre
             "pkmom_grid_bytes", "pkmom_assign_scratch_bytes", "pkmom_footprint_bytes", "pkmom_assign",
             "pkmom_fft", "pkmom_spectra", "pkmom_estimate", "pkmom_estimate_host", "pkmom_sync",
             "pkmom_timing_enable", "pkmom_timing_read", "pkmom_kernel_launches", "pkmom_spectra_static",
-            "pkmom_set_tuning", "pkmom_assign_scratch_bytes_tuned")
+            "pkmom_set_tuning", "pkmom_assign_scratch_bytes_tuned", "pkmom_spectra_mu")
 
 
 def params(box_L: float, ng: int, nbins: int, *, order: int = 4, precision: int = F32, kmin_kf: float = 1.0,
@@ -222,6 +227,32 @@ class Context:
         self._check(lib().pkmom_spectra(self._h, ctypes.byref(p), grids.data_ptr(), moments.data_ptr(),
                                         out.data_ptr(), _stream_ptr(stream)))
 
+    def spectra_mu(self, p: Params, grids, moments, nmu: int, direction=None, out=None, stream=None):
+        """pkmom_spectra_mu: spectra in (|k|, mu) bins; returns a (MU_NROWS, nbins * nmu)
+        float64 CUDA tensor. direction: 3 numbers, or None for the bulk flow."""
+        import torch
+        if out is None:
+            out = torch.empty((MU_NROWS, p.nbins * nmu), dtype=torch.float64, device=grids.device)
+        d = None if direction is None else (ctypes.c_double * 3)(*[float(x) for x in direction])
+        self._check(lib().pkmom_spectra_mu(self._h, ctypes.byref(p), grids.data_ptr(), moments.data_ptr(), d,
+                                           int(nmu), out.data_ptr(), _stream_ptr(stream)))
+        return out
+
+    def estimate_mu(self, pos, vel, p: Params, nmu: int, direction=None, mass=None, stream=None):
+        """Moments, deposit and FFT (pkmom_assign, pkmom_fft) into fresh device buffers,
+        then pkmom_spectra_mu; returns the (MU_NROWS, nbins * nmu) tensor."""
+        import torch
+        cat = catalog_from_tensors(pos, vel, mass)
+        dt = torch.float32 if p.precision == F32 else torch.float64
+        item = 4 if p.precision == F32 else 8
+        dev = pos.device
+        grids = torch.empty(Context.grid_bytes(p.ng, p.precision) // item, dtype=dt, device=dev)
+        mom = torch.zeros(16, dtype=torch.float64, device=dev)
+        scratch = torch.empty(self.scratch_bytes_tuned(p, cat.n), dtype=torch.uint8, device=dev)
+        self.assign(cat, p, grids, mom, scratch, stream=stream)
+        self.fft(p, grids, stream=stream)
+        return self.spectra_mu(p, grids, mom, nmu, direction=direction, stream=stream)
+
     def estimate(self, pos, vel, p: Params, mass=None, out=None, stream=None):
         """All steps on device tensors; returns a (NROWS, nbins) float64 CUDA tensor."""
         import torch
@@ -272,6 +303,12 @@ def spectra_static(p: Params, grids, moments, out, stream=None):
                                     _stream_ptr(stream))
     if st != 0:
         raise PkmomError(st, lib().pkmom_strerror(st).decode())
+
+
+def as_mu_dict(out, nbins: int, nmu: int) -> dict:
+    """(MU_NROWS, nbins * nmu) array/tensor -> {row name: (nbins, nmu) numpy array}."""
+    a = out.detach().cpu().numpy() if hasattr(out, "detach") else np.asarray(out)
+    return {k: a[i].reshape(nbins, nmu) for k, i in MU_ROW.items()}
 
 
 def as_dict(out) -> dict:
