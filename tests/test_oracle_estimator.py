@@ -13,7 +13,7 @@ from paper_2005_06170_gb300 import catalogs
 
 # ---------------------------------------------------------------- assignment
 
-@pytest.mark.parametrize("order", [1, 2, 3, 4])
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 5])
 def test_deposit_conserves_each_field(order):
     rng = np.random.default_rng(3)
     u = rng.uniform(-20, 40, size=(300, 3))
@@ -84,7 +84,7 @@ def test_truncated_bl_estimate_converges_to_the_exact_kernel():
     assert dev[16] < 1e-4, dev
 
 
-@pytest.mark.parametrize("order", [3, 4])
+@pytest.mark.parametrize("order", [3, 4, 5])
 def test_factored_bl_equals_direct_real_space_bl(order):
     """The oracle's BL field (B-spline deposit x periodic Fourier factor) equals the
     deposit with phi itself, summed over periodic images (direct, no Fourier factor)."""
@@ -164,14 +164,14 @@ def _lattice_expected(ng, L, kint, amp, order=4):
     V = L ** 3
     val = V * amp ** 2 / 4.0
     samples = {4: lambda w: (2 + np.cos(w)) / 3.0, 2: lambda w: np.ones_like(w), 1: lambda w: np.ones_like(w),
-               3: lambda w: (3 + np.cos(w)) / 4.0}
+               3: lambda w: (3 + np.cos(w)) / 4.0, 5: lambda w: (115 + 76 * np.cos(w) + np.cos(2 * w)) / 192.0}
     for a in range(3):
         w = 2 * np.pi * kint[a] / ng
         val *= (samples[order](np.array(w)) / bs.bspline_hat(w, order)) ** 2
     return float(val)
 
 
-@pytest.mark.parametrize("order", [4, 3, 2])
+@pytest.mark.parametrize("order", [5, 4, 3, 2])
 @pytest.mark.parametrize("kint,e,kind", [((1, 2, 0), (2, -1, 0), "curl"), ((1, 2, 0), (1, 2, 0), "grad"),
                                          ((0, 0, 3), (0, 0, 1), "grad"), ((2, 1, 1), (0, 1, -1), "curl")])
 def test_lattice_plane_wave_closed_form(order, kint, e, kind):
@@ -203,6 +203,13 @@ def test_b3_integer_samples():
     np.testing.assert_allclose(v, [1 / 8, 3 / 4, 1 / 8], atol=1e-15)
 
 
+def test_b5_integer_samples():
+    # the (115 + 76 cos w + cos 2w)/192 used above: the centred quartic B-spline at the
+    # integers is (1/384, 19/96, 115/192, 19/96, 1/384) (textbook values)
+    v = bs.bspline(np.arange(-2.0, 3.0), 5)
+    np.testing.assert_allclose(v, [1 / 384, 19 / 96, 115 / 192, 19 / 96, 1 / 384], atol=1e-15)
+
+
 # ---------------------------------------------------------------- Poisson shot noise
 
 def _z_scores(out, key, sn_key, n_modes):
@@ -212,7 +219,7 @@ def _z_scores(out, key, sn_key, n_modes):
     return out[key] / sigma
 
 
-@pytest.mark.parametrize("order", [4, 1])
+@pytest.mark.parametrize("order", [5, 4, 1])
 def test_poisson_catalog_deconvolved_spectra_vanish(order):
     """Eq. psn / rawPp: for a Poisson catalogue the raw spectrum is pure shot noise,
     so the deconvolved, noise-subtracted spectra scatter around zero. (NGP, order 1,

@@ -40,7 +40,7 @@ def test_integer_samples_sum_to_one(m):
         assert sum(bs.bspline_int_samples(m).values()) == 1
 
 
-@pytest.mark.parametrize("m", [1, 2, 3, 4])
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 5])
 def test_bspline_partition_of_unity_and_integral(m):
     x = np.linspace(-0.5, 0.5, 101)
     s = sum(bs.bspline(x - n, m) for n in range(-6, 7))
@@ -50,7 +50,7 @@ def test_bspline_partition_of_unity_and_integral(m):
     assert abs(integral - 1.0) < 1e-5  # trapezoid error at the box edges ~ h/2
 
 
-@pytest.mark.parametrize("m", [2, 3, 4])
+@pytest.mark.parametrize("m", [2, 3, 4, 5])
 def test_bspline_convolution_recursion(m):
     # B_m = B_{m-1} * B_1 by numerical convolution on a fine grid
     h = 1e-3
@@ -62,7 +62,7 @@ def test_bspline_convolution_recursion(m):
     assert np.max(np.abs(conv - lhs)) < 5e-3
 
 
-@pytest.mark.parametrize("m", [2, 3, 4])
+@pytest.mark.parametrize("m", [2, 3, 4, 5])
 def test_bspline_hat_is_fourier_transform(m):
     # direct quadrature of int B_m(x) cos(w x) dx
     x = np.linspace(-m / 2, m / 2, 40001)
@@ -71,7 +71,7 @@ def test_bspline_hat_is_fourier_transform(m):
         assert abs(ft - bs.bspline_hat(w, m)) < 1e-7
 
 
-@pytest.mark.parametrize("m", [2, 3, 4])
+@pytest.mark.parametrize("m", [2, 3, 4, 5])
 def test_alias_sum_closed_form_vs_brute_force(m):
     w = np.linspace(-np.pi, np.pi, 41)
     np.testing.assert_allclose(bs.alias_sum(w, m), bs.alias_sum_brute(w, m, jmax=4000), rtol=0, atol=1e-12)
@@ -93,7 +93,7 @@ def test_alias_sums_match_jing2005():
         np.testing.assert_allclose(bs.alias_sum(w, int(order)), ref, atol=1e-15)
 
 
-@pytest.mark.parametrize("m", [1, 2, 3, 4])
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 5])
 def test_phi_hat_orthonormal_and_partition(m):
     w = np.linspace(-np.pi, np.pi, 29)
     np.testing.assert_allclose(bs.phi_alias_sum_brute(w, m, jmax=400 if m > 1 else 20000), 1.0,
@@ -128,7 +128,7 @@ def test_phi_decay_of_bl3_coefficients():
     assert abs(c[30]) < 1e-7 and abs(c[40]) < 1e-9
 
 
-@pytest.mark.parametrize("m", [2, 3, 4])
+@pytest.mark.parametrize("m", [2, 3, 4, 5])
 def test_phi_alias_sum_brute_force_converges_to_closed_form(m):
     w = np.linspace(-np.pi, np.pi, 17)
     err = np.abs(bs.phi_alias_sum_brute(w, m, jmax=3000) - bs.phi_alias_sum(w, m))
