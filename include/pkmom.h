@@ -126,7 +126,10 @@ typedef struct {
 typedef struct {
     double box_L;            /* side of the periodic box (> 0) */
     int ng;                  /* grid points per side: a multiple of 8 in 16..1024 */
-    int order;               /* B-spline order m of the BL kernel: 1..4 (4 = BL3, default) */
+    int order;               /* B-spline order m of the BL kernel: 1..5 (4 = BL3, default). With
+                                the exact deconvolution the order-m estimate equals that of the
+                                plain order-m B-spline with its exact alias-sum shot noise (5: the
+                                fifth-order B-spline the paper compares BL3 with, Sec. 2.4.1) */
     int precision;           /* PKMOM_F32 (FP32 grids and FFT) or PKMOM_F64 */
     int nbins;               /* number of linear |k| shells, 1..1024 */
     double kmin_kf;          /* shell range in units of k_f = 2 pi / L; kmin_kf <= 0 means 1 */

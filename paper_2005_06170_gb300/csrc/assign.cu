@@ -326,6 +326,21 @@ __device__ __forceinline__ void bspline_weights(T t, T (&w)[M], int &first)
         w[2] = (T(-3) * t3 + T(3) * t2 + T(3) * t + T(1)) * sixth;
         w[3] = t3 * sixth;
         first = -1;
+    } else if constexpr (M == 5) {
+        // the centred quartic B-spline at distances d + 2 .. d - 2 from the nearest node
+        const bool up = t >= T(0.5);
+        const T d = up ? t - T(1) : t;  // offset from the nearest node, in [-1/2, 1/2)
+        const T d2 = d * d;
+        auto mid = [](T x) {  // 1/2 <= x <= 3/2
+            return (T(55) + x * (T(20) + x * (T(-120) + x * (T(80) + x * T(-16))))) / T(96);
+        };
+        const T lo = T(1) - T(2) * d, hi = T(1) + T(2) * d;
+        w[0] = lo * lo * lo * lo / T(384);
+        w[1] = mid(T(1) + d);
+        w[2] = T(115) / T(192) - T(5) / T(8) * d2 + T(0.25) * d2 * d2;
+        w[3] = mid(T(1) - d);
+        w[4] = hi * hi * hi * hi / T(384);
+        first = up ? -1 : -2;
     } else if constexpr (M == 3) {
         const bool up = t >= T(0.5);
         const T d = up ? t - T(1) : t;  // offset from the nearest node, in [-1/2, 1/2)
@@ -386,7 +401,8 @@ struct DepositCfg {
 
 // Largest product of three B-spline weights of order M: bounds any node value of the
 // tile by this times (particles in the tile's reach) times max |q|.
-template <int M> constexpr float kMaxWeight3 = M == 4 ? 0.2962963f : (M == 3 ? 0.421875f : 1.0f);
+template <int M> constexpr float kMaxWeight3 =
+    M == 5 ? 0.2148770f : (M == 4 ? 0.2962963f : (M == 3 ? 0.421875f : 1.0f));
 // The same for the BL function: max |phi| = phi(0) = 1.0890, cubed 1.2916.
 constexpr float kMaxWeight3BL = 1.2917f;
 template <int M, int BLR> constexpr float kMaxW3 = BLR > 0 ? kMaxWeight3BL : kMaxWeight3<M>;
@@ -1531,6 +1547,7 @@ cudaError_t launch_deposit(const AssignPlan &pl, void *scratch, void *grids, cud
     case 2: e = launch_deposit_m<2>(pl, offsets, qmax, rec, grids, halo, s); break;
     case 3: e = launch_deposit_m<3>(pl, offsets, qmax, rec, grids, halo, s); break;
     case 4: e = launch_deposit_m<4>(pl, offsets, qmax, rec, grids, halo, s); break;
+    case 5: e = launch_deposit_m<5>(pl, offsets, qmax, rec, grids, halo, s); break;
     default: return cudaErrorInvalidValue;
     }
     st.launches += (pl.tile == kHomeTile && pl.order == 4) ? 2 : 1;

@@ -93,7 +93,7 @@ pkmom_status check_params(pkmom_ctx *ctx, const pkmom_params *p)
     if (!p) return fail(ctx, PKMOM_EINVAL, "params is NULL");
     if (!(p->box_L > 0) || !std::isfinite(p->box_L)) return fail(ctx, PKMOM_EINVAL, "box_L must be > 0");
     if (p->ng < 16 || p->ng > 1024 || p->ng % 8) return fail(ctx, PKMOM_EINVAL, "ng must be a multiple of 8 in [16, 1024]");
-    if (p->order < 1 || p->order > 4) return fail(ctx, PKMOM_EINVAL, "order must be 1..4");
+    if (p->order < 1 || p->order > 5) return fail(ctx, PKMOM_EINVAL, "order must be 1..5");
     if (p->precision != PKMOM_F32 && p->precision != PKMOM_F64) return fail(ctx, PKMOM_EINVAL, "bad precision");
     if (p->nbins < 1 || p->nbins > 1024) return fail(ctx, PKMOM_EINVAL, "nbins must be 1..1024");
     const double lo = umin_of(*p), hi = umax_of(*p);

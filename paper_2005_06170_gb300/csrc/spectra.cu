@@ -467,11 +467,14 @@ const double *euler_frobenius(int m)
     static const double b4[] = {2.0 / 3.0, 1.0 / 6.0};
     static const double b6[] = {11.0 / 20.0, 13.0 / 60.0, 1.0 / 120.0};
     static const double b8[] = {151.0 / 315.0, 397.0 / 1680.0, 1.0 / 42.0, 1.0 / 5040.0};
+    static const double b10[] = {15619.0 / 36288.0, 44117.0 / 181440.0, 913.0 / 22680.0, 251.0 / 181440.0,
+                                 1.0 / 362880.0};
     switch (m) {
     case 1: return b2;
     case 2: return b4;
     case 3: return b6;
     case 4: return b8;
+    case 5: return b10;
     default: return nullptr;
     }
 }
@@ -712,6 +715,8 @@ __device__ const double kEF1[1] = {1.0};
 __device__ const double kEF2[2] = {2.0 / 3.0, 1.0 / 6.0};
 __device__ const double kEF3[3] = {11.0 / 20.0, 13.0 / 60.0, 1.0 / 120.0};
 __device__ const double kEF4[4] = {151.0 / 315.0, 397.0 / 1680.0, 1.0 / 42.0, 1.0 / 5040.0};
+__device__ const double kEF5[5] = {15619.0 / 36288.0, 44117.0 / 181440.0, 913.0 / 22680.0, 251.0 / 181440.0,
+                                   1.0 / 362880.0};
 
 // The shell table and the per-axis window factors, built on the device in FP64 with
 // the same expressions as build_spectra_tables (correctly rounded sqrt and division,
@@ -721,7 +726,7 @@ __global__ void k_static_tables(int ng, int order, bool direct, int nbins, doubl
                                 uint16_t *__restrict__ bintab, T *__restrict__ gf, T *__restrict__ gh,
                                 double *__restrict__ hf, double *__restrict__ hh)
 {
-    const double *ef = order == 1 ? kEF1 : order == 2 ? kEF2 : order == 3 ? kEF3 : kEF4;
+    const double *ef = order == 1 ? kEF1 : order == 2 ? kEF2 : order == 3 ? kEF3 : order == 4 ? kEF4 : kEF5;
     const int nh = ng / 2 + 1;
     const int stride = gridDim.x * blockDim.x;
     for (int nsq = blockIdx.x * blockDim.x + threadIdx.x; nsq <= nsq_max; nsq += stride) {
@@ -815,7 +820,7 @@ extern "C" pkmom_status pkmom_spectra_static(const pkmom_params *p, const void *
 {
     using namespace pkmom;
     if (!p || !grids || !moments_dev || !out_dev) return PKMOM_EINVAL;
-    if (!(p->box_L > 0) || p->ng < 16 || p->ng > 1024 || p->ng % 8 || p->order < 1 || p->order > 4 ||
+    if (!(p->box_L > 0) || p->ng < 16 || p->ng > 1024 || p->ng % 8 || p->order < 1 || p->order > 5 ||
         (p->precision != PKMOM_F32 && p->precision != PKMOM_F64) || p->nbins < 1 || p->theta_sn_mode < 0 ||
         p->theta_sn_mode > 1 || (p->bl_radius != 0 && (p->bl_radius < 2 || p->bl_radius > 4 || p->order != 4)))
         return PKMOM_EINVAL;

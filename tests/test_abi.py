@@ -41,8 +41,9 @@ def test_params_default_and_sizes():
     assert pkmom.Context.footprint_bytes(p, 256 ** 3) > s + pkmom.Context.grid_bytes(256, 0)
 
 
-@pytest.mark.parametrize("bad", [dict(ng=20), dict(ng=8), dict(nbins=0), dict(kmax_kf=200.0), dict(order=5),
-                                 dict(box_L=-1.0)])
+@pytest.mark.parametrize("bad", [dict(ng=20), dict(ng=8), dict(nbins=0), dict(kmax_kf=200.0), dict(order=6),
+                                 dict(box_L=-1.0), dict(bl_radius=1), dict(bl_radius=5),
+                                 dict(order=3, bl_radius=2)])
 def test_invalid_params_have_no_scratch_size(bad):
     kw = dict(box_L=100.0, ng=64, nbins=8)
     kw.update({k: v for k, v in bad.items() if k in kw})

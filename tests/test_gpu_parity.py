@@ -113,7 +113,7 @@ def test_moments_match_oracle(ctx, gpu_lib, dtype):
     assert m[14] == len(cat["pos"])
 
 
-@pytest.mark.parametrize("order", [1, 2, 3, 4])
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("dtype,ng", [(np.float32, 32), (np.float64, 24), (np.float32, 40)])
 def test_assigned_grids_match_oracle(ctx, gpu_lib, order, dtype, ng):
     import torch
@@ -221,7 +221,7 @@ def test_ragged_fp32_masses_odd_order(ctx, gpu_lib):
     compare(g, o, 1e-4)
 
 
-@pytest.mark.parametrize("order", [1, 2, 4])
+@pytest.mark.parametrize("order", [1, 2, 4, 5])
 def test_orders_fp64(ctx, gpu_lib, order):
     pk = gpu_lib
     L = 64.0
