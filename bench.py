@@ -457,20 +457,39 @@ def main(argv=None):
             "gpu_launches": int(launches), "clocks": clk}
 
     if rank == 0 and not args.no_e2e:
-        # end to end through the C-ABI with pinned host buffers: H2D of the catalogue,
-        # the estimate, D2H of the spectra, every step
+        # end to end through the public host API with pinned host buffers: every step
+        # copies its catalogue in and reads its spectra back. HostPipeline copies
+        # catalogue i+1 while catalogue i is estimated (the link moves ~210 GB/s, about
+        # the estimate's own pace at this size); pkmom_estimate_host (one call per step,
+        # copies not overlapped) is reported beside it.
+        from paper_2005_06170_gb300.pipeline import HostPipeline
         hp = torch.from_numpy(cat["pos"]).pin_memory()
         hv = torch.from_numpy(cat["vel"]).pin_memory()
         hout = torch.empty((pkmom.NROWS, nbins), dtype=torch.float64).pin_memory()
+        k_e = max(3, min(args.steps, 10))
+        pipe = HostPipeline(n_max=n, nbins_max=nbins, precision=p.precision)
+        pipe.submit(hp, hv, p).result()  # warm-up: plans, tables, buffers
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        prev = None
+        for _ in range(k_e):
+            cur = pipe.submit(hp, hv, p)
+            if prev is not None:
+                prev.result()
+            prev = cur
+        prev.result()
+        dt = (time.perf_counter() - t0) / k_e
+        pipe.close()
         hpn, hvn, hon = hp.numpy(), hv.numpy(), hout.numpy()
         ctx.estimate_host(hpn, hvn, p, out=hon, stream=stream)
-        k_e = max(3, min(args.steps, 10))
-        t0 = time.perf_counter()
+        t1 = time.perf_counter()
         for _ in range(k_e):
             ctx.estimate_host(hpn, hvn, p, out=hon, stream=stream)
-        dt = (time.perf_counter() - t0) / k_e
+        dt1 = (time.perf_counter() - t1) / k_e
         line["e2e"] = {"value": n / dt, "unit": "particles/s", "h2d_bytes_per_step": int(hp.nbytes + hv.nbytes),
-                       "d2h_bytes_per_step": int(hout.nbytes), "ms_per_step": dt * 1e3, "steps": k_e}
+                       "d2h_bytes_per_step": int(hout.nbytes), "ms_per_step": dt * 1e3, "steps": k_e,
+                       "api": "HostPipeline (copy of step i+1 overlaps the estimate of step i)",
+                       "single_call": {"value": n / dt1, "ms_per_step": dt1 * 1e3, "api": "pkmom_estimate_host"}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cat, args.workload)
     ctx.close()
