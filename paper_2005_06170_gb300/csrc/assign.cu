@@ -1238,34 +1238,54 @@ k_deposit_home(const Record<float> *__restrict__ rec, const uint32_t *__restrict
 }
 
 // Owned nodes within reach of a neighbouring tile's particles (local index 0, 1 or 15
-// on some axis) receive that neighbour's halo values, added in a fixed order.
+// on some axis) receive that neighbour's halo values, added in a fixed order. Threads
+// take only those 1899 nodes of a tile: the x faces (x in {0, 1, 15}), then the y faces
+// of the other x, then the z faces of the rest, z fastest where a face allows.
+constexpr int kHomeEdge = 3 * kHomeT * kHomeT + (kHomeT - 3) * 3 * kHomeT + (kHomeT - 3) * (kHomeT - 3) * 3;
+__device__ __forceinline__ int home_face(int s) { return s == 2 ? kHomeT - 1 : s; }  // 0, 1, 15
+
 __global__ void __launch_bounds__(256)
 k_home_fixup(const float *__restrict__ halo, int ng, float *__restrict__ grids, int64_t grid_elems)
 {
     const int nt = ng / kHomeT;
     const int tz = blockIdx.x % nt, ty = (blockIdx.x / nt) % nt, tx = blockIdx.x / (nt * nt);
     auto wrap = [nt](int a) { return a < 0 ? a + nt : (a >= nt ? a - nt : a); };
-    auto edge = [](int l) { return l <= 1 || l == kHomeT - 1; };
-    // offsets d on one axis whose tile's halo covers local index l: 0, -1 (l = 0, 1), +1 (l = 15)
-    auto dlo = [](int l) { return l <= 1 ? -1 : 0; };
-    auto dhi = [](int l) { return l == kHomeT - 1 ? 1 : 0; };
-    for (int k = threadIdx.x; k < kHomeT * kHomeT * kHomeT; k += blockDim.x) {
-        const int z = k & 15, y = (k >> 4) & 15, x = k >> 8;
-        if (!(edge(x) || edge(y) || edge(z))) continue;
+    // the neighbour offset on one axis whose halo covers local index l (0 if none)
+    auto side = [](int l) { return l <= 1 ? -1 : (l == kHomeT - 1 ? 1 : 0); };
+    constexpr int nx = 3 * kHomeT * kHomeT, ny = (kHomeT - 3) * 3 * kHomeT;
+    for (int k = threadIdx.x; k < kHomeEdge; k += blockDim.x) {
+        int x, y, z;
+        if (k < nx) {
+            x = home_face(k / (kHomeT * kHomeT));
+            y = (k / kHomeT) % kHomeT;
+            z = k % kHomeT;
+        } else if (k < nx + ny) {
+            const int r = k - nx;
+            x = 2 + r / (3 * kHomeT);
+            y = home_face((r / kHomeT) % 3);
+            z = r % kHomeT;
+        } else {
+            const int r = k - nx - ny;
+            x = 2 + r / (3 * (kHomeT - 3));
+            y = 2 + (r / 3) % (kHomeT - 3);
+            z = home_face(r % 3);
+        }
         const int64_t gi = (static_cast<int64_t>(tx * kHomeT + x) * ng + (ty * kHomeT + y)) * (ng + 2) + tz * kHomeT + z;
         float v[4];
 #pragma unroll
         for (int f = 0; f < 4; ++f) v[f] = grids[f * grid_elems + gi];
-        for (int dx = dlo(x); dx <= dhi(x); ++dx)
-            for (int dy = dlo(y); dy <= dhi(y); ++dy)
-                for (int dz = dlo(z); dz <= dhi(z); ++dz) {
-                    if (dx == 0 && dy == 0 && dz == 0) continue;
-                    const int nb = (wrap(tx + dx) * nt + wrap(ty + dy)) * nt + wrap(tz + dz);
-                    const int hi = home_halo_index(x - kHomeT * dx + 1, y - kHomeT * dy + 1, z - kHomeT * dz + 1);
-                    const float *hp = halo + static_cast<int64_t>(nb) * 4 * kHomeHalo + hi;
+        const int sx = side(x), sy = side(y), sz = side(z);
+        // neighbours (dx, dy, dz), each 0 or the axis' side, in a fixed order
 #pragma unroll
-                    for (int f = 0; f < 4; ++f) v[f] += hp[f * kHomeHalo];
-                }
+        for (int c = 1; c < 8; ++c) {
+            const int dx = (c & 4) ? sx : 0, dy = (c & 2) ? sy : 0, dz = (c & 1) ? sz : 0;
+            if (((c & 4) && !sx) || ((c & 2) && !sy) || ((c & 1) && !sz)) continue;
+            const int nb = (wrap(tx + dx) * nt + wrap(ty + dy)) * nt + wrap(tz + dz);
+            const int hi = home_halo_index(x - kHomeT * dx + 1, y - kHomeT * dy + 1, z - kHomeT * dz + 1);
+            const float *hp = halo + static_cast<int64_t>(nb) * 4 * kHomeHalo + hi;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) v[f] += hp[f * kHomeHalo];
+        }
 #pragma unroll
         for (int f = 0; f < 4; ++f) grids[f * grid_elems + gi] = v[f];
     }
