@@ -241,7 +241,7 @@ pkmom_status pkmom_sync(pkmom_ctx *ctx, void *stream);
  * every pkmom_assign/fft/spectra call records start/stop events around each
  * stage; pkmom_timing_read synchronises on the last events and returns the
  * accumulated milliseconds and call counts per stage, then resets them.
- * Stages: 0 moments+histogram, 1 scan, 2 scatter (sort), 3 deposit, 4 FFT,
+ * Stages: 0 histogram, 1 scan, 2 scatter (sort) and moments, 3 deposit, 4 FFT,
  * 5 deconvolution+binning, 6 finalize. */
 enum { PKMOM_STAGE_HIST = 0, PKMOM_STAGE_SCAN, PKMOM_STAGE_SCATTER, PKMOM_STAGE_DEPOSIT,
        PKMOM_STAGE_FFT, PKMOM_STAGE_BIN, PKMOM_STAGE_FINAL, PKMOM_NSTAGES };

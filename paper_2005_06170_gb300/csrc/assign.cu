@@ -3,18 +3,19 @@
 // Eq. rawFFTed; the BL kernel's Fourier factor is applied in spectra.cu).
 //
 // Pipeline (all on one stream):
-//   k_hist_moments  one pass over the catalogue: FP64 moments (block partials) and a
-//                   histogram of sort keys (key = x-row, y-row, z-segment of the cell).
-//   k_moments_final fixed-order sum of the block partials -> pkmom_moments.
+//   k_hist          the histogram of sort keys (key = x-row, y-row, z-segment of the
+//                   cell), from the positions alone.
 //   k_scan_*        exclusive scan of the key counts -> segment offsets.
 //   k_scatter       writes each particle as a 32-byte record (grid coordinates and the
 //                   four deposited values) at the slot an atomic increment of its key's
 //                   cursor returns: a counting sort (any order within a key).
-//   k_deposit       one CTA per output tile of grid nodes: gathers the particles of
-//                   every segment whose stencils reach the tile (tile + halo, located
-//                   through the offsets), accumulates B-spline weights x values in
-//                   shared memory, then writes each node of the tile exactly once.
-//                   No global atomics, no zero-fill pass.
+//   k_moments       FP64 moments (block partials) and max |q|, from velocities and masses.
+//   k_moments_final fixed-order sum of the block partials -> pkmom_moments.
+//   k_deposit_home  (FP32, cubic, >= 1/2 particle per cell) each particle deposited
+//   + k_home_fixup  once by the tile owning its cell, halos added afterwards; otherwise
+//   k_deposit(_fx)  one CTA per output tile gathers the particles of every segment whose
+//                   stencils reach the tile, accumulates in shared memory, then writes
+//                   each node of the tile exactly once. No global atomics, no zero fill.
 #include <cfloat>
 #include <cmath>
 #include <mutex>
@@ -60,99 +61,28 @@ template <> __device__ __forceinline__ double pack_cell<double>(int c0, int c1, 
 __device__ __forceinline__ int unpack_cell(float v) { return __float_as_int(v); }
 __device__ __forceinline__ int unpack_cell(double v) { return static_cast<int>(v); }
 
-// One pass over the catalogue: the histogram of sort keys and the moments. Each lane sums kGroup
-// particles in the catalogue precision; the warp then adds its lanes' group sums
-// (shuffles) and lane 0 adds the result to FP64 accumulators, so that FP64 work is
-// one add per value per 32 * kGroup particles. Two particles per iteration keep more
-// loads and atomics in flight.
+// The histogram of sort keys: positions only (12 bytes per FP32 particle), one
+// fire-and-forget atomic increment per particle; non-finite or huge positions raise
+// the data error flag. Two particles per iteration keep more loads in flight.
 template <typename T>
-__global__ void __launch_bounds__(kHistThreads, 4)
-k_hist_moments(const T *__restrict__ x, const T *__restrict__ y, const T *__restrict__ z,
-               const T *__restrict__ vx, const T *__restrict__ vy, const T *__restrict__ vz,
-               const T *__restrict__ mass, int64_t stride, int64_t n, T scale, int ng, int sshift,
-               uint32_t *__restrict__ counts, double *__restrict__ partials,
-               unsigned *__restrict__ qmax_bits, int *__restrict__ err)
+__global__ void __launch_bounds__(kHistThreads)
+k_hist(const T *__restrict__ x, const T *__restrict__ y, const T *__restrict__ z, int64_t stride, int64_t n,
+       T scale, int ng, int sshift, uint32_t *__restrict__ counts, int *__restrict__ err)
 {
     const int nseg = ng >> sshift;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ double s_part[kHistThreads / 32][kMomentVals];  // per-warp FP64 sums
-    if (lane < kMomentVals) s_part[warp][lane] = 0.0;
-    __syncwarp();
-    float qmax[4] = {0.f, 0.f, 0.f, 0.f};
-    T grp[kMomentVals];
-#pragma unroll
-    for (int k = 0; k < kMomentVals; ++k) grp[k] = T(0);
-    int gcount = 0;
     const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    const int64_t wbase0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31);
-
-    auto flush = [&]() {
-#pragma unroll
-        for (int k = 0; k < kMomentVals; ++k) {
-            T v = grp[k];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) s_part[warp][k] += static_cast<double>(v);
-            grp[k] = T(0);
-        }
-    };
     auto one = [&](int64_t i) {
         const int64_t j = i * stride;
         const T u0 = mul_rn(x[j], scale), u1 = mul_rn(y[j], scale), u2 = mul_rn(z[j], scale);
-        const T m = mass ? mass[i] : T(1);
-        const T v0 = vx[j], v1 = vy[j], v2 = vz[j];
         int c0, c1, c2;
-        const bool ok = cell_of(u0, ng, c0) & cell_of(u1, ng, c1) & cell_of(u2, ng, c2);
-        if (ok) {
-            const int64_t key = (static_cast<int64_t>(c0) * ng + c1) * nseg + (c2 >> sshift);
-            atomicAdd(counts + key, 1u);  // no value returned: the scatter takes the slots
-        } else {
+        if (cell_of(u0, ng, c0) & cell_of(u1, ng, c1) & cell_of(u2, ng, c2))
+            atomicAdd(counts + (static_cast<int64_t>(c0) * ng + c1) * nseg + (c2 >> sshift), 1u);
+        else
             *err = 1;
-        }
-        const T m2 = m * m;
-        qmax[0] = fmaxf(qmax[0], static_cast<float>(fabs(m)));
-        qmax[1] = fmaxf(qmax[1], static_cast<float>(fabs(m * v0)));
-        qmax[2] = fmaxf(qmax[2], static_cast<float>(fabs(m * v1)));
-        qmax[3] = fmaxf(qmax[3], static_cast<float>(fabs(m * v2)));
-        grp[0] += m;
-        grp[1] += m2;
-        grp[2] += m * v0;
-        grp[3] += m * v1;
-        grp[4] += m * v2;
-        grp[5] += m2 * v0;
-        grp[6] += m2 * v1;
-        grp[7] += m2 * v2;
-        grp[8] += m2 * v0 * v0;
-        grp[9] += m2 * v1 * v1;
-        grp[10] += m2 * v2 * v2;
-        grp[11] += m2 * v0 * v1;
-        grp[12] += m2 * v0 * v2;
-        grp[13] += m2 * v1 * v2;
     };
-    // warp-uniform loop: every lane runs the same iterations (shuffles inside)
-    for (int64_t wb = wbase0; wb < n; wb += 2 * step) {
-        const int64_t i0 = wb + lane, i1 = wb + step + lane;
-        if (i0 < n) one(i0);
-        if (i1 < n) one(i1);
-        gcount += 2;
-        if (gcount >= kGroup) {
-            flush();
-            gcount = 0;
-        }
-    }
-    flush();
-
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        // non-negative floats order like their bit patterns
-        const unsigned b = __reduce_max_sync(0xffffffffu, __float_as_uint(qmax[f]));
-        if (lane == 0) atomicMax(qmax_bits + f, b);
-    }
-    __syncthreads();
-    if (threadIdx.x < kMomentVals) {
-        double s = 0.0;
-        for (int w = 0; w < kHistThreads / 32; ++w) s += s_part[w][threadIdx.x];
-        partials[static_cast<int64_t>(blockIdx.x) * kMomentWords + threadIdx.x] = s;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += 2 * step) {
+        one(i);
+        if (i + step < n) one(i + step);
     }
 }
 
@@ -288,7 +218,183 @@ k_scan_apply(uint32_t *__restrict__ counts, int64_t nkeys, const uint32_t *__res
     }
 }
 
+// ------------------------------------------------------------------ moments
+// The catalogue moments and the largest |q| of each deposited field, from velocities
+// and masses alone: each lane sums kGroup particles in the catalogue precision (four
+// per iteration, loads issued first), the warp adds its lanes' group sums (shuffles)
+// and lane 0 adds them to FP64 accumulators, so that FP64 work is one add per value
+// per 32 * kGroup particles; block sums go to partials[block] (k_moments_final).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_moments(const T *__restrict__ vx, const T *__restrict__ vy, const T *__restrict__ vz, const T *__restrict__ mass,
+          int64_t stride, int64_t n, double *__restrict__ partials, unsigned *__restrict__ qmax_bits)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ double s_part[256 / 32][kMomentVals];  // per-warp FP64 sums
+    if (lane < kMomentVals) s_part[warp][lane] = 0.0;
+    __syncwarp();
+    float qmax[4] = {0.f, 0.f, 0.f, 0.f};
+    T grp[kMomentVals];
+#pragma unroll
+    for (int k = 0; k < kMomentVals; ++k) grp[k] = T(0);
+    int gcount = 0;
+    const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    auto flush = [&]() {
+#pragma unroll
+        for (int k = 0; k < kMomentVals; ++k) {
+            T v = grp[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) s_part[warp][k] += static_cast<double>(v);
+            grp[k] = T(0);
+        }
+    };
+    auto add = [&](T m, T v0, T v1, T v2) {
+        const T m2 = m * m;
+        qmax[0] = fmaxf(qmax[0], static_cast<float>(fabs(m)));
+        qmax[1] = fmaxf(qmax[1], static_cast<float>(fabs(m * v0)));
+        qmax[2] = fmaxf(qmax[2], static_cast<float>(fabs(m * v1)));
+        qmax[3] = fmaxf(qmax[3], static_cast<float>(fabs(m * v2)));
+        grp[0] += m;
+        grp[1] += m2;
+        grp[2] += m * v0;
+        grp[3] += m * v1;
+        grp[4] += m * v2;
+        grp[5] += m2 * v0;
+        grp[6] += m2 * v1;
+        grp[7] += m2 * v2;
+        grp[8] += m2 * v0 * v0;
+        grp[9] += m2 * v1 * v1;
+        grp[10] += m2 * v2 * v2;
+        grp[11] += m2 * v0 * v1;
+        grp[12] += m2 * v0 * v2;
+        grp[13] += m2 * v1 * v2;
+    };
+    // warp-uniform loop: every lane runs the same iterations (shuffles inside)
+    for (int64_t wb = static_cast<int64_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); wb < n; wb += 4 * step) {
+        T m[4], a[4], b[4], c[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = wb + k * step + lane;
+            const bool ok = i < n;
+            const int64_t j = ok ? i * stride : 0;
+            m[k] = ok ? (mass ? mass[i] : T(1)) : T(0);  // absent particles add nothing
+            a[k] = ok ? vx[j] : T(0);
+            b[k] = ok ? vy[j] : T(0);
+            c[k] = ok ? vz[j] : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) add(m[k], a[k], b[k], c[k]);
+        gcount += 4;
+        if (gcount >= kGroup) {
+            flush();
+            gcount = 0;
+        }
+    }
+    flush();
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        // non-negative floats order like their bit patterns
+        const unsigned bits = __reduce_max_sync(0xffffffffu, __float_as_uint(qmax[f]));
+        if (lane == 0) atomicMax(qmax_bits + f, bits);
+    }
+    __syncthreads();
+    if (threadIdx.x < kMomentVals) {
+        double sum = 0.0;
+        for (int w = 0; w < 256 / 32; ++w) sum += s_part[w][threadIdx.x];
+        partials[static_cast<int64_t>(blockIdx.x) * kMomentWords + threadIdx.x] = sum;
+    }
+}
+
+// FP32 interleaved (n, 3) velocities, 16-byte aligned: four particles per thread read
+// as three 128-bit loads ((v0x v0y v0z v1x) (v1y v1z v2x v2y) (v2z v3x v3y v3z)), and
+// four masses as one. The same sums as k_moments; the n % 4 last particles are added
+// by the first lanes of block 0.
+__global__ void __launch_bounds__(256)
+k_moments_v3(const float *__restrict__ v, const float *__restrict__ mass, int64_t n,
+             double *__restrict__ partials, unsigned *__restrict__ qmax_bits)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ double s_part[256 / 32][kMomentVals];
+    if (lane < kMomentVals) s_part[warp][lane] = 0.0;
+    __syncwarp();
+    float qmax[4] = {0.f, 0.f, 0.f, 0.f};
+    float grp[kMomentVals];
+#pragma unroll
+    for (int k = 0; k < kMomentVals; ++k) grp[k] = 0.f;
+    int gcount = 0;
+    const int64_t nq = n / 4;
+    const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const float4 *v4 = reinterpret_cast<const float4 *>(v);
+    const float4 *m4 = reinterpret_cast<const float4 *>(mass);
+    auto flush = [&]() {
+#pragma unroll
+        for (int k = 0; k < kMomentVals; ++k) {
+            float x = grp[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) s_part[warp][k] += static_cast<double>(x);
+            grp[k] = 0.f;
+        }
+    };
+    auto add = [&](float m, float v0, float v1, float v2) {
+        const float m2 = m * m;
+        qmax[0] = fmaxf(qmax[0], fabsf(m));
+        qmax[1] = fmaxf(qmax[1], fabsf(m * v0));
+        qmax[2] = fmaxf(qmax[2], fabsf(m * v1));
+        qmax[3] = fmaxf(qmax[3], fabsf(m * v2));
+        grp[0] += m;
+        grp[1] += m2;
+        grp[2] += m * v0;
+        grp[3] += m * v1;
+        grp[4] += m * v2;
+        grp[5] += m2 * v0;
+        grp[6] += m2 * v1;
+        grp[7] += m2 * v2;
+        grp[8] += m2 * v0 * v0;
+        grp[9] += m2 * v1 * v1;
+        grp[10] += m2 * v2 * v2;
+        grp[11] += m2 * v0 * v1;
+        grp[12] += m2 * v0 * v2;
+        grp[13] += m2 * v1 * v2;
+    };
+    for (int64_t wb = static_cast<int64_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); wb < nq; wb += step) {
+        const int64_t q = wb + lane;
+        if (q < nq) {
+            const float4 a = v4[3 * q], b = v4[3 * q + 1], c = v4[3 * q + 2];
+            const float4 mm = mass ? m4[q] : make_float4(1.f, 1.f, 1.f, 1.f);
+            add(mm.x, a.x, a.y, a.z);
+            add(mm.y, a.w, b.x, b.y);
+            add(mm.z, b.z, b.w, c.x);
+            add(mm.w, c.y, c.z, c.w);
+        }
+        gcount += 4;
+        if (gcount >= kGroup) {
+            flush();
+            gcount = 0;
+        }
+    }
+    if (blockIdx.x == 0 && warp == 0) {
+        const int64_t i = 4 * nq + lane;
+        if (i < n) add(mass ? mass[i] : 1.f, v[3 * i], v[3 * i + 1], v[3 * i + 2]);
+    }
+    flush();
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const unsigned bits = __reduce_max_sync(0xffffffffu, __float_as_uint(qmax[f]));
+        if (lane == 0) atomicMax(qmax_bits + f, bits);
+    }
+    __syncthreads();
+    if (threadIdx.x < kMomentVals) {
+        double sum = 0.0;
+        for (int w = 0; w < 256 / 32; ++w) sum += s_part[w][threadIdx.x];
+        partials[static_cast<int64_t>(blockIdx.x) * kMomentWords + threadIdx.x] = sum;
+    }
+}
+
 // ------------------------------------------------------------------ scatter
+// Each particle is written as a 32-byte record at the slot an atomic increment of its
+// key's cursor returns: a counting sort (any order within a key).
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_scatter(const T *__restrict__ x, const T *__restrict__ y, const T *__restrict__ z, const T *__restrict__ vx,
@@ -301,7 +407,7 @@ k_scatter(const T *__restrict__ x, const T *__restrict__ y, const T *__restrict_
         const int64_t j = i * stride;
         const T u0 = mul_rn(x[j], scale), u1 = mul_rn(y[j], scale), u2 = mul_rn(z[j], scale);
         int c0, c1, c2;
-        if (!(cell_of(u0, ng, c0) & cell_of(u1, ng, c1) & cell_of(u2, ng, c2))) continue;  // reported by the histogram
+        if (!(cell_of(u0, ng, c0) & cell_of(u1, ng, c1) & cell_of(u2, ng, c2))) continue;  // reported by k_hist
         const int64_t key = (static_cast<int64_t>(c0) * ng + c1) * nseg + (c2 >> sshift);
         const uint32_t dst = atomicAdd(cursor + key, 1u);
         const T m = mass ? mass[i] : T(1);
@@ -1474,23 +1580,20 @@ cudaError_t launch_hist_moments(const pkmom_catalog &cat, const AssignPlan &pl, 
 {
     char *sc = static_cast<char *>(scratch);
     uint32_t *counts = key_table(pl, scratch);
-    auto *partials = reinterpret_cast<double *>(sc + pl.off_partials);
     auto *qmax = reinterpret_cast<unsigned *>(sc + pl.off_qmax);
     cudaError_t e = cudaMemsetAsync(sc + pl.off_counts, 0, key_table_bytes(pl.nkeys), s);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(qmax, 0, 4 * sizeof(unsigned), s);
+    e = cudaMemsetAsync(qmax, 0, 4 * sizeof(unsigned), s);  // maxima taken by the scatter
     if (e != cudaSuccess) return e;
     const double scale = static_cast<double>(pl.ng) / box_L;
     if (pl.prec == PKMOM_F32) {
-        k_hist_moments<float><<<pl.hist_blocks, kHistThreads, 0, s>>>(
-            tp<float>(cat.x), tp<float>(cat.y), tp<float>(cat.z), tp<float>(cat.vx), tp<float>(cat.vy),
-            tp<float>(cat.vz), tp<float>(cat.mass), cat.stride, cat.n, static_cast<float>(scale), pl.ng, pl.sshift,
-            counts, partials, qmax, err_flag);
+        k_hist<float><<<pl.hist_blocks, kHistThreads, 0, s>>>(tp<float>(cat.x), tp<float>(cat.y), tp<float>(cat.z),
+                                                            cat.stride, cat.n, static_cast<float>(scale), pl.ng,
+                                                            pl.sshift, counts, err_flag);
     } else {
-        k_hist_moments<double><<<pl.hist_blocks, kHistThreads, 0, s>>>(
-            tp<double>(cat.x), tp<double>(cat.y), tp<double>(cat.z), tp<double>(cat.vx), tp<double>(cat.vy),
-            tp<double>(cat.vz), tp<double>(cat.mass), cat.stride, cat.n, scale, pl.ng, pl.sshift, counts,
-            partials, qmax, err_flag);
+        k_hist<double><<<pl.hist_blocks, kHistThreads, 0, s>>>(tp<double>(cat.x), tp<double>(cat.y),
+                                                             tp<double>(cat.z), cat.stride, cat.n, scale, pl.ng,
+                                                             pl.sshift, counts, err_flag);
     }
     st.launches++;
     return cudaGetLastError();
@@ -1524,21 +1627,34 @@ cudaError_t launch_scatter(const pkmom_catalog &cat, const AssignPlan &pl, doubl
 {
     char *sc = static_cast<char *>(scratch);
     uint32_t *cursor = key_table(pl, scratch);
+    auto *partials = reinterpret_cast<double *>(sc + pl.off_partials);
+    auto *qmax = reinterpret_cast<unsigned *>(sc + pl.off_qmax);
     const double scale = static_cast<double>(pl.ng) / box_L;
-    const unsigned blocks = pl.hist_blocks;
+    const unsigned blocks = pl.hist_blocks;  // k_moments: one partial per block
     if (pl.prec == PKMOM_F32) {
         k_scatter<float><<<blocks, 256, 0, s>>>(tp<float>(cat.x), tp<float>(cat.y), tp<float>(cat.z),
                                                 tp<float>(cat.vx), tp<float>(cat.vy), tp<float>(cat.vz),
                                                 tp<float>(cat.mass), cat.stride, cat.n, static_cast<float>(scale),
                                                 pl.ng, pl.sshift, cursor,
                                                 reinterpret_cast<Record<float> *>(sc + pl.off_records));
+        const char *bv = static_cast<const char *>(cat.vx);
+        const bool v3 = cat.stride == 3 && static_cast<const char *>(cat.vy) == bv + 4 &&
+                        static_cast<const char *>(cat.vz) == bv + 8 && reinterpret_cast<uintptr_t>(bv) % 16 == 0 &&
+                        (!cat.mass || reinterpret_cast<uintptr_t>(cat.mass) % 16 == 0);
+        if (v3)
+            k_moments_v3<<<blocks, 256, 0, s>>>(tp<float>(cat.vx), tp<float>(cat.mass), cat.n, partials, qmax);
+        else
+            k_moments<float><<<blocks, 256, 0, s>>>(tp<float>(cat.vx), tp<float>(cat.vy), tp<float>(cat.vz),
+                                                    tp<float>(cat.mass), cat.stride, cat.n, partials, qmax);
     } else {
         k_scatter<double><<<blocks, 256, 0, s>>>(tp<double>(cat.x), tp<double>(cat.y), tp<double>(cat.z),
                                                  tp<double>(cat.vx), tp<double>(cat.vy), tp<double>(cat.vz),
                                                  tp<double>(cat.mass), cat.stride, cat.n, scale, pl.ng, pl.sshift,
-                                                 cursor,
-                                                 reinterpret_cast<Record<double> *>(sc + pl.off_records));
+                                                 cursor, reinterpret_cast<Record<double> *>(sc + pl.off_records));
+        k_moments<double><<<blocks, 256, 0, s>>>(tp<double>(cat.vx), tp<double>(cat.vy), tp<double>(cat.vz),
+                                                 tp<double>(cat.mass), cat.stride, cat.n, partials, qmax);
     }
+    st.launches++;
     st.launches++;
     return cudaGetLastError();
 }

@@ -423,9 +423,7 @@ pkmom_status pkmom_assign(pkmom_ctx *ctx, const pkmom_catalog *cat, const pkmom_
     cudaStream_t st = as_stream(stream);
     {
         StageTimer t(ctx, PKMOM_STAGE_HIST, st);
-        PK_CUDA(launch_hist_moments(*cat, pl, p->box_L, scratch, ctx->d_err, st, ctx->st), "moments/histogram");
-        PK_CUDA(launch_moments_final(pl, cat->n, scratch, static_cast<double *>(moments_dev), st, ctx->st),
-                "moments");
+        PK_CUDA(launch_hist_moments(*cat, pl, p->box_L, scratch, ctx->d_err, st, ctx->st), "histogram");
     }
     {
         StageTimer t(ctx, PKMOM_STAGE_SCAN, st);
@@ -433,7 +431,9 @@ pkmom_status pkmom_assign(pkmom_ctx *ctx, const pkmom_catalog *cat, const pkmom_
     }
     {
         StageTimer t(ctx, PKMOM_STAGE_SCATTER, st);
-        PK_CUDA(launch_scatter(*cat, pl, p->box_L, scratch, st, ctx->st), "scatter");
+        PK_CUDA(launch_scatter(*cat, pl, p->box_L, scratch, st, ctx->st), "scatter and moments");
+        PK_CUDA(launch_moments_final(pl, cat->n, scratch, static_cast<double *>(moments_dev), st, ctx->st),
+                "moments");
     }
     {
         StageTimer t(ctx, PKMOM_STAGE_DEPOSIT, st);
