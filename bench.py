@@ -50,7 +50,11 @@ DEFAULT = "zeldovich256_ng256"
 # DRAM bytes (read + write) per launch of the dominant stage's kernels, from one ncu
 # capture of the current kernels (profiles/kernels_zeldovich256_ng256.md); a stage
 # whose kernels change drops its entry until it is captured again
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    ("zeldovich256_ng256", "deposit"): ((617.650432 + 409.996544 + 458.1888 + 171.559168) * 1e6,
+                                        "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_deposit_home and "
+                                        "k_home_fixup, one launch each (profiles/kernels_zeldovich256_ng256.md)"),
+}
 # configs 4 and 5 run through their own drivers below
 MULTI = {
     "batch64": "64 catalogues in one launch sequence: particle counts log-uniform in [1e5, 2e7], seeded "
