@@ -19,6 +19,8 @@
 #include <cfloat>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
+#include <utility>
 
 #include "pkmom_internal.cuh"
 
@@ -43,6 +45,18 @@ __device__ __forceinline__ bool cell_of(T u, int ng, int &c)
     }
     c = ic;
     return true;
+}
+
+// f(std::integral_constant<int, i>) for i = 0 .. N - 1, each i a compile-time constant
+template <class F, int... I>
+__device__ __forceinline__ void static_for_seq(F &&f, std::integer_sequence<int, I...>)
+{
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_for(F &&f)
+{
+    static_for_seq(f, std::make_integer_sequence<int, N>{});
 }
 
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
@@ -421,9 +435,22 @@ k_scatter(const T *__restrict__ x, const T *__restrict__ y, const T *__restrict_
 // ------------------------------------------------------------------ deposit
 // B-spline weights of order M for a particle at fractional offset t = u - floor(u)
 // in its cell; `first` receives the first node relative to floor(u).
+// Offset from floor(u) of the first of the M nodes the order-M B-spline reaches for a
+// particle at offset t in its cell (the convention of bspline_weights below).
+template <int M, typename T>
+__device__ __forceinline__ int bspline_first(T t)
+{
+    if constexpr (M == 5) return t >= T(0.5) ? -1 : -2;
+    else if constexpr (M == 4) return -1;
+    else if constexpr (M == 3) return t >= T(0.5) ? 0 : -1;
+    else if constexpr (M == 2) return 0;
+    else return t >= T(0.5) ? 1 : 0;
+}
+
 template <int M, typename T>
 __device__ __forceinline__ void bspline_weights(T t, T (&w)[M], int &first)
 {
+    first = bspline_first<M, T>(t);
     if constexpr (M == 4) {
         const T s = T(1) - t, t2 = t * t, t3 = t2 * t;
         const T sixth = T(1) / T(6);
@@ -431,7 +458,6 @@ __device__ __forceinline__ void bspline_weights(T t, T (&w)[M], int &first)
         w[1] = (T(3) * t3 - T(6) * t2 + T(4)) * sixth;
         w[2] = (T(-3) * t3 + T(3) * t2 + T(3) * t + T(1)) * sixth;
         w[3] = t3 * sixth;
-        first = -1;
     } else if constexpr (M == 5) {
         // the centred quartic B-spline at distances d + 2 .. d - 2 from the nearest node
         const bool up = t >= T(0.5);
@@ -446,7 +472,6 @@ __device__ __forceinline__ void bspline_weights(T t, T (&w)[M], int &first)
         w[2] = T(115) / T(192) - T(5) / T(8) * d2 + T(0.25) * d2 * d2;
         w[3] = mid(T(1) - d);
         w[4] = hi * hi * hi * hi / T(384);
-        first = up ? -1 : -2;
     } else if constexpr (M == 3) {
         const bool up = t >= T(0.5);
         const T d = up ? t - T(1) : t;  // offset from the nearest node, in [-1/2, 1/2)
@@ -454,14 +479,11 @@ __device__ __forceinline__ void bspline_weights(T t, T (&w)[M], int &first)
         w[0] = T(0.5) * a * a;
         w[1] = T(0.75) - d * d;
         w[2] = T(0.5) * b * b;
-        first = up ? 0 : -1;
     } else if constexpr (M == 2) {
         w[0] = T(1) - t;
         w[1] = t;
-        first = 0;
     } else {
         w[0] = T(1);
-        first = t >= T(0.5) ? 1 : 0;
     }
 }
 
@@ -797,7 +819,7 @@ __device__ __forceinline__ void tile_scales(float bound, float cmax, bool cells,
 template <int T0, int T1, int T2, int NT>
 __device__ __forceinline__ void deposit_cells_path(const Record<float> *__restrict__ rec,
                                                    const uint32_t *__restrict__ offsets, int ng, int t0, int t1, int t2,
-                                                   int *acc, int fstride, int rw, const float *s_fine,
+                                                   int *acc, int fstride, int px, int rw, const float *s_fine,
                                                    const int *s_shift)
 {
     constexpr int HL = 2, R0 = T0 + 3, R1 = T1 + 3, RZ = T2 + 3, NW = NT / 32;
@@ -821,7 +843,7 @@ __device__ __forceinline__ void deposit_cells_path(const Record<float> *__restri
         const int lxa = cx - 1 + dxl, lxb = lxa + 2, ly = cy - 1 + dy, lz = cz - 1 + dz;
         const bool yz = ly >= 0 && ly < T1 && lz >= 0 && lz < T2;
         const bool ina = yz && lxa >= 0 && lxa < T0, inb = yz && lxb >= 0 && lxb < T0;
-        const int oa = (lxa * T1 + ly) * rw + lz, ob = ((lxa + 2) * T1 + ly) * rw + lz;
+        const int oa = lxa * px + ly * rw + lz, ob = (lxa + 2) * px + ly * rw + lz;
         for (uint32_t i0 = beg; i0 < end; i0 += kCellFlush) {
             int a[4], b[4];
             cell_chunk(rec, i0, min(end, i0 + kCellFlush), pc, fine, shift, a, b);
@@ -834,14 +856,112 @@ __device__ __forceinline__ void deposit_cells_path(const Record<float> *__restri
     }
 }
 
+// Shared accumulator of the FP32 gather deposit: int[4][T0][PX] per tile, node (x, y, z)
+// at x * PX + y * RW + z. The row pitch RW = T2 + 1 is odd; the plane pitch PX = T1 * RW
+// + 3 is odd as well, so that the bank of a node, (x PX + y RW + z) mod 32, mixes all
+// three coordinates (with PX = 16 mod 32, as T1 * RW alone would give for 16 x 17, x
+// would add only its parity).
+//
+// The listed path adds every stencil node of every particle, with the weights of nodes
+// outside the tile set to zero (an add of exactly 0), at an address formed by the same
+// linear rule; such a node lies at most 5 nodes below or 4 above the tile on each axis
+// (orders 1 to 5), so the allocation has FRONT words of padding before the accumulator
+// and at least BACK words after it (the particle list or padding). The zero adds land on
+// padding, on other nodes or on list entries, and change none of them.
+template <int T0, int T1, int T2>
+struct FxLayout {
+    static constexpr int RW = T2 + 1;
+    static constexpr int PX = T1 * RW + 3;
+    static constexpr int TNP = T0 * PX;  // ints per field
+    static constexpr int FRONT = (5 * (PX + RW + 1) + 3) / 4 * 4;
+    static constexpr int BACK = 4 * PX + (T1 + 4) * RW + T2 + 5;
+    static size_t bytes(int list_cap)
+    {
+        return size_t(FRONT + 4 * TNP + (list_cap > BACK ? list_cap : BACK)) * sizeof(int);
+    }
+};
+
+// Four shared-memory adds at byte offsets OFF + f * FS (f = 0..3) from addr (the offsets
+// are immediates).
+template <int OFF, int FS>
+__device__ __forceinline__ void red4(unsigned addr, int v0, int v1, int v2, int v3)
+{
+    asm volatile(
+        "red.shared.add.s32 [%0+%5], %1;\n\t"
+        "red.shared.add.s32 [%0+%6], %2;\n\t"
+        "red.shared.add.s32 [%0+%7], %3;\n\t"
+        "red.shared.add.s32 [%0+%8], %4;" ::"r"(addr),
+        "r"(v0), "r"(v1), "r"(v2), "r"(v3), "n"(OFF), "n"(OFF + FS), "n"(OFF + 2 * FS), "n"(OFF + 3 * FS));
+}
+
+// Tile-local coordinates of the first stencil node of a particle in the tile's reach,
+// where no periodic wrap falls inside the reach (ng >= tile + M cells): the cell offset
+// from the tile's corner is taken into [-HL, T + HR).
+template <int M, int HL, int HR, int T>
+__device__ __forceinline__ int first_node(float t, int cell, int corner, int ng)
+{
+    int d = cell - corner;
+    d = d < -HL ? d + ng : (d >= T + HR ? d - ng : d);
+    return d + bspline_first<M, float>(t);
+}
+
+// One particle of the reordered list (see k_deposit_fx): its M^3 stencil nodes at
+// immediate offsets from the shared-window address of its first node, with the weights of
+// nodes outside the tile set to zero (no branch or predicate per node; see FxLayout). The
+// contributions of the nodes in the tile are those of the per-node path.
+template <int M, int T0, int T1, int T2, int HL, int HR>
+__device__ __forceinline__ void banked_particle(const Record<float> &r, int ng, int t0, int t1, int t2, unsigned acc_s,
+                                                float sc0, float sc1, float sc2, float sc3)
+{
+    using Lay = FxLayout<T0, T1, T2>;
+    constexpr int RW = Lay::RW, PX = Lay::PX, TNP = Lay::TNP;
+    constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+    constexpr int kMagicBits = 0x4B400000;
+    const int packed = unpack_cell(r.u.w);
+    float w[3][M];
+    int first;
+    bspline_weights<M, float>(r.u.x, w[0], first);
+    bspline_weights<M, float>(r.u.y, w[1], first);
+    bspline_weights<M, float>(r.u.z, w[2], first);
+    const int b0 = first_node<M, HL, HR, T0>(r.u.x, packed & 1023, t0, ng);
+    const int b1 = first_node<M, HL, HR, T1>(r.u.y, (packed >> 10) & 1023, t1, ng);
+    const int b2 = first_node<M, HL, HR, T2>(r.u.z, (packed >> 20) & 1023, t2, ng);
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        w[0][k] = static_cast<unsigned>(b0 + k) < static_cast<unsigned>(T0) ? w[0][k] : 0.0f;
+        w[1][k] = static_cast<unsigned>(b1 + k) < static_cast<unsigned>(T1) ? w[1][k] : 0.0f;
+        w[2][k] = static_cast<unsigned>(b2 + k) < static_cast<unsigned>(T2) ? w[2][k] : 0.0f;
+    }
+    // (the first node may lie below the accumulator, inside the front padding)
+    const unsigned base = acc_s + 4u * static_cast<unsigned>(b0 * PX + b1 * RW + b2);
+    const float q0 = r.q.x * sc0, q1 = r.q.y * sc1, q2 = r.q.z * sc2, q3 = r.q.w * sc3;
+    auto row = [&](auto k0c, auto k1c) {
+        constexpr int k0 = decltype(k0c)::value, k1 = decltype(k1c)::value;
+        const float w01 = w[0][k0] * w[1][k1];
+        auto node = [&](auto k2c) {
+            constexpr int k2 = decltype(k2c)::value;
+            const float ww = w01 * w[2][k2];
+            red4<4 * (k0 * PX + k1 * RW + k2), 4 * TNP>(base, __float_as_int(fmaf(q0, ww, kMagic)) - kMagicBits,
+                                                        __float_as_int(fmaf(q1, ww, kMagic)) - kMagicBits,
+                                                        __float_as_int(fmaf(q2, ww, kMagic)) - kMagicBits,
+                                                        __float_as_int(fmaf(q3, ww, kMagic)) - kMagicBits);
+        };
+        static_for<M>(node);
+    };
+    static_for<M>([&](auto k0c) { static_for<M>([&](auto k1c) { row(k0c, k1c); }); });
+}
+
 // Tile-gather deposit for FP32 grids with 32-bit integer (fixed-point) shared-memory
 // atomics (about three times the throughput of FP32 shared atomics on this part).
 //
-// Work split: each warp walks its own contiguous chunk of the tile's particle list 32
-// at a time, lane j taking the j-th particle of each step. Sorted neighbours lie in
-// neighbouring cells, so for one stencil offset the lanes mostly hit different nodes
-// (particles that share a cell still collide). Rows of the shared accumulator are
-// padded to an odd length.
+// Work split: tiles whose reach holds few particles (sparse catalogues) list them in
+// shared memory, reordered so that 32 consecutive entries have their first stencil nodes
+// in different banks, and warps take consecutive chunks of 32 (banked_particle: every
+// node at an immediate offset, nodes outside the tile adding exactly 0). Other
+// tiles: each warp walks its own contiguous chunk of the tile's particle list 32 at a
+// time, lane j taking the j-th particle of each step, node by node; tiles with more than
+// two particles per reach cell (cubic order) take the cell-block path. The accumulator
+// layout is FxLayout.
 //
 // Fixed point: field f of the tile uses the scale 2^s_f with
 //   B_f 2^s_f < 2^30,   B_f = w3 * min(M^2 * largest row count, particle count) * max |q_f|
@@ -852,23 +972,30 @@ __device__ __forceinline__ void deposit_cells_path(const Record<float> *__restri
 // nearest even, one rounding of the exact product). The bound depends only on counts
 // and maxima, and integer sums do not depend on order: the grids are the same whatever
 // order the sort leaves particles of one cell in.
+constexpr int kListRankMax = 128;  // largest bank group whose list entries are reordered
+
+// (16^3-cell and larger tiles: up to 128 registers, as shared memory already holds them to
+// two per SM; 8^3 tiles: 64, for eight per SM)
 template <int M, int T0, int T1, int T2, int NT, int BLR = 0>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (NT >= 256 ? 2 : 8))
 k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__ offsets,
              const unsigned *__restrict__ qmax_bits, int ng, int sshift, float *__restrict__ grids, int64_t grid_elems,
              int list_cap)
 {
     using C = DepositCfg<float, M, T0, T1, T2, NT>;
-    constexpr int RW = T2 + 1;  // odd row pitch
-    constexpr int TNP = T0 * T1 * RW;
+    using Lay = FxLayout<T0, T1, T2>;
+    constexpr int RW = Lay::RW, PX = Lay::PX, TNP = Lay::TNP;
     constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    int *acc = reinterpret_cast<int *>(smem_raw);  // [4][T0 * T1][RW]
+    int *acc = reinterpret_cast<int *>(smem_raw) + Lay::FRONT;  // [4][T0][PX], FxLayout
     __shared__ uint32_t s_beg[C::MAXR];
     __shared__ uint32_t s_pre[C::MAXR + 1];
     __shared__ unsigned s_rowmax;
     __shared__ float s_scale[4], s_fine[4];
     __shared__ int s_shift[4];
+    __shared__ uint32_t s_bank[33];       // listed path: bank group counts, then the largest
+    __shared__ uint32_t s_rbase[kListRankMax];  // entries before rank r of the reordered list
+    __shared__ unsigned s_rmask[kListRankMax];  // bank groups with more than r entries
 
     const int ntz = ng / T2, nty = ng / T1;
     int tile = blockIdx.x;
@@ -877,7 +1004,7 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
     const int ty = tile % nty;
     const int tx = tile / nty;
     const int t0 = tx * T0, t1 = ty * T1, t2 = tz * T2;
-    for (int k = threadIdx.x; k < 4 * TNP; k += NT) acc[k] = 0;
+    for (int k = threadIdx.x; k < TNP; k += NT) reinterpret_cast<int4 *>(acc)[k] = make_int4(0, 0, 0, 0);
     if (threadIdx.x == 0) s_rowmax = 0;
     const uint32_t total = build_ranges<C>(offsets, ng, sshift, t0, t1, t2, T2, s_beg, s_pre);
     if (BLR > 0 && sshift == 0) {
@@ -951,10 +1078,88 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
     constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
     constexpr int kMagicBits = 0x4B400000;
 
+    // Listed tiles with no periodic wrap inside the reach (ng >= tile + M cells) take the
+    // listed path of banked_particle: every stencil node at an immediate offset from the
+    // first node, nodes outside the tile adding exactly 0. A node's bank is the
+    // first node's plus a constant, so the list is reordered by (rank within its bank
+    // group, bank group): 32 consecutive entries then hold distinct first-node banks, or
+    // span two ranks (at most two adds per bank), and warps take consecutive chunks of 32
+    // (every lane busy). Each contribution is the same rounded integer as on the per-node
+    // path, so the grids do not depend on the order.
+    constexpr int KP = 8;       // listed particles placed per thread
+    const bool banked = BLR == 0 && listed && !dense && total <= static_cast<uint32_t>(KP * NT) && sshift == 0 &&
+                        ng >= C::R0 && ng >= C::R1 && ng >= T2 + C::HL + C::HR;
+    if (banked) {
+        if (threadIdx.x < 32) s_bank[threadIdx.x] = 0;
+        __syncthreads();
+        Vec4<float> u[KP];
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            const uint32_t p = threadIdx.x + k * NT;
+            if (p < total) u[k] = rec[s_idx[p]].u;
+        }
+        int key[KP];  // bank group | rank << 5, -1 for no particle
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            key[k] = -1;
+            if (threadIdx.x + k * NT < total) {
+                const int packed = unpack_cell(u[k].w);
+                const int b0 = first_node<M, C::HL, C::HR, T0>(u[k].x, packed & 1023, t0, ng);
+                const int b1 = first_node<M, C::HL, C::HR, T1>(u[k].y, (packed >> 10) & 1023, t1, ng);
+                const int b2 = first_node<M, C::HL, C::HR, T2>(u[k].z, (packed >> 20) & 1023, t2, ng);
+                const int g = (b0 * PX + b1 * RW + b2) & 31;
+                key[k] = g | static_cast<int>(atomicAdd(&s_bank[g], 1u) << 5);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const uint32_t mx = __reduce_max_sync(0xffffffffu, s_bank[lane]);
+            if (lane == 0) s_bank[32] = mx;
+        }
+        __syncthreads();
+        const uint32_t maxc = s_bank[32];
+        if (maxc <= static_cast<uint32_t>(kListRankMax)) {
+            // entries before (r, g): sum over groups of min(count, r), then the groups
+            // below g with more than r entries
+            for (uint32_t r = warp; r < maxc; r += NW) {
+                const uint32_t c = s_bank[lane];
+                const unsigned m = __ballot_sync(0xffffffffu, c > r);
+                const uint32_t below = __reduce_add_sync(0xffffffffu, c < r ? c : r);
+                if (lane == 0) s_rmask[r] = m, s_rbase[r] = below;
+            }
+            uint32_t idx[KP];
+#pragma unroll
+            for (int k = 0; k < KP; ++k) idx[k] = key[k] >= 0 ? s_idx[threadIdx.x + k * NT] : 0u;
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+                if (key[k] < 0) continue;
+                const int g = key[k] & 31, r = key[k] >> 5;
+                s_idx[s_rbase[r] + __popc(s_rmask[r] & ((1u << g) - 1u))] = idx[k];
+            }
+            __syncthreads();
+        }
+    }
+
     bool cells_done = false;
+    if constexpr (BLR == 0) {
+        if (banked) {
+            const unsigned acc_s = static_cast<unsigned>(__cvta_generic_to_shared(acc));
+            uint32_t p = threadIdx.x;  // warp w takes chunks w, w + NW, ... of 32 entries
+            Record<float> nxt;
+            if (p < total) nxt = rec[s_idx[p]];
+            while (p < total) {
+                const Record<float> rc = nxt;
+                p += NT;
+                if (p < total) nxt = rec[s_idx[p]];
+                banked_particle<M, T0, T1, T2, C::HL, C::HR>(rc, ng, t0, t1, t2, acc_s, sc0, sc1, sc2, sc3);
+            }
+            cells_done = true;
+        }
+    }
     if constexpr (M == 4 && BLR == 0) {  // the cell-block path uses B-spline pieces
         if (dense) {
-            deposit_cells_path<T0, T1, T2, NT>(rec, offsets, ng, t0, t1, t2, acc, TNP, RW, s_fine, s_shift);
+            deposit_cells_path<T0, T1, T2, NT>(rec, offsets, ng, t0, t1, t2, acc, TNP, PX, RW, s_fine, s_shift);
             cells_done = true;
         }
     }
@@ -973,7 +1178,7 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
                 for (int k1 = 0; k1 < M; ++k1) {
                     if (li[1][k1] < 0) continue;
                     const float w01 = wx * w[1][k1];
-                    const int b01 = (lx * T1 + li[1][k1]) * RW;
+                    const int b01 = lx * PX + li[1][k1] * RW;
 #pragma unroll
                     for (int k2 = 0; k2 < M; ++k2) {
                         if (li[2][k2] < 0) continue;
@@ -1007,7 +1212,7 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
         const int l2 = k % T2, l01 = k / T2;
         const int l1 = l01 % T1, l0 = l01 / T1;
         const int64_t gi = (static_cast<int64_t>(t0 + l0) * ng + (t1 + l1)) * (ng + 2) + t2 + l2;
-        const int ai = l01 * RW + l2;
+        const int ai = l0 * PX + l1 * RW + l2;
 #pragma unroll
         for (int f = 0; f < 4; ++f) grids[f * grid_elems + gi] = static_cast<float>(acc[f * TNP + ai]) * inv[f];
     }
@@ -1450,7 +1655,7 @@ cudaError_t launch_deposit_t(const AssignPlan &pl, const uint32_t *offsets, cons
     if constexpr (sizeof(T) == 4) {
         kern = k_deposit_fx<M, T0, T1, T2, NT, BLR>;
         list_cap = pl.list_cap;
-        smem = size_t(4) * T0 * T1 * (T2 + 1) * sizeof(int) + size_t(list_cap) * sizeof(uint32_t);
+        smem = FxLayout<T0, T1, T2>::bytes(list_cap);
     } else {
         kern = k_deposit<T, M, T0, T1, T2, NT, BLR>;
     }
