@@ -253,8 +253,9 @@ def run_batch64(args):
 
 
 def run_serve(args):
-    """Config 5: a Poisson arrival stream served with continuous batching (4 lanes,
-    admission by footprint against 180 GB) and, on the same trace, one request at a
+    """Config 5: a Poisson arrival stream served with continuous batching (4 lanes, one
+    of them for large requests; admission by footprint against 180 GB) and, on the same
+    trace, one request at a
     time (1 lane): throughput and p50/p99 latency of both."""
     import threading
 

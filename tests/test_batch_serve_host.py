@@ -45,6 +45,26 @@ def test_admission_bounds_overtaking():
     assert [r.rid for r in pol.admit(q, free_lanes=2, in_use=0)] == [0]
 
 
+def test_admission_strict_lane_kinds():
+    """Separate lanes for large requests: a large request starts only on a free large
+    lane and a small one only on a free small lane; waiting for its kind of lane is not
+    an overtake."""
+    pol = AdmissionPolicy(budget_bytes=1000, max_overtake=1)
+    large = lambda r: r.footprint > 100  # noqa: E731
+    q = [_req(500, 0), _req(10, 1), _req(20, 2), _req(400, 3), _req(30, 4)]
+    got = pol.admit(q, free_lanes=3, in_use=0, free_large=1, is_large=large)
+    assert [r.rid for r in got] == [0, 1, 2]  # one large lane, two small ones
+    assert q[3].overtaken == 0
+    rest = [q[3], q[4]]
+    got = pol.admit(rest, free_lanes=2, in_use=500, free_large=0, is_large=large)
+    assert [r.rid for r in got] == [4]  # the large lane is busy: the large request waits
+    assert q[3].overtaken == 0
+    for _ in range(3):  # lane-bound waits never make it block the small requests
+        assert [r.rid for r in pol.admit(rest, free_lanes=2, in_use=500, free_large=0, is_large=large)] == [4]
+    got = pol.admit(rest, free_lanes=1, in_use=500, free_large=1, is_large=large)
+    assert [r.rid for r in got] == [3]
+
+
 def test_admission_respects_memory_in_use():
     pol = AdmissionPolicy(budget_bytes=100)
     q = [_req(40, 0)]

@@ -109,6 +109,38 @@ def test_served_results_same_alone_and_in_the_mix(gpu_lib):
         np.testing.assert_allclose(b, a, rtol=1e-12, atol=1e-12 * np.nanmax(np.abs(a)), equal_nan=True)
 
 
+def test_large_requests_keep_their_own_lane(gpu_lib):
+    """Strict lanes: requests above large_bytes run only on the last lane, one at a time
+    and in arrival order; the others never take that lane; every result equals the one
+    computed alone."""
+    import torch
+
+    from paper_2005_06170_gb300.serve import Request, Server
+    pk = gpu_lib
+    items = _mixed(seed=7)[:6]
+    devs = [_dev(c, torch) for c, _, _ in items]
+    params = [pk.params(L, 64 if k % 2 else 32, 8) for k, (_, L, _) in enumerate(items)]
+    srv = Server(lanes=1)
+    alone = [srv.submit(Request(d["pos"], d["vel"], p)).result(timeout=120) for d, p in zip(devs, params)]
+    fps = [srv.footprint(Request(d["pos"], d["vel"], p)) for d, p in zip(devs, params)]
+    srv.close()
+    cut = (max(f for f, p in zip(fps, params) if p.ng == 32) + min(f for f, p in zip(fps, params) if p.ng == 64)) / 2
+    assert max(f for f, p in zip(fps, params) if p.ng == 32) < cut < min(f for f, p in zip(fps, params) if p.ng == 64)
+    srv = Server(lanes=3, large_bytes=cut)
+    futs = [srv.submit(Request(d["pos"], d["vel"], p)) for d, p in zip(devs, params)]
+    mixed = [f.result(timeout=120) for f in futs]
+    done = list(srv.completed)
+    srv.close()
+    large = sorted((r for r in done if r.footprint > cut), key=lambda r: r.admitted)
+    assert large and all(r.lane == 2 for r in large)
+    assert all(r.lane in (0, 1) for r in done if r.footprint <= cut)
+    assert [r.rid for r in large] == sorted(r.rid for r in large)  # arrival order
+    for a, b in zip(large, large[1:]):
+        assert b.admitted >= a.done - 1e-3  # never two large ones at once
+    for a, b in zip(alone, mixed):
+        np.testing.assert_allclose(b, a, rtol=1e-12, atol=1e-12 * np.nanmax(np.abs(a)), equal_nan=True)
+
+
 def test_serving_admits_by_footprint(gpu_lib):
     import torch
 
