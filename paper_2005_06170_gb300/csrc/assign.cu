@@ -1332,11 +1332,85 @@ __device__ __forceinline__ void home_particle(int *acc, const Record<float> &r, 
     }
 }
 
-// A sorted particle of this tile (its cell read from the record); skipped if the record
-// does not lie in the tile.
-__device__ __forceinline__ void home_listed(int *acc, const Record<float> &r, int t0, int t1, int t2, float sc0,
-                                            float sc1, float sc2, float sc3)
+// The first particles of four z-consecutive home cells (z = 4m .. 4m + 3 of column
+// (cx, cy)) of one lane. For each of the 16 (x, y) stencil node columns the lane sums
+// the cells' contributions to the 7 z nodes it reaches in registers, then adds the 7
+// sums: 28 shared adds per node column instead of 64 for four particles one by one.
+// Each contribution is the same rounded integer as in home_particle (same products, one
+// FFMA against 1.5 * 2^23); the raw bit patterns are summed modulo 2^32 and the magic
+// constant is taken off once per node (cnt(i) cells reach z node i), so the sums are
+// exact. An empty cell has q = 0 and adds exactly the magic constant. With the lanes of
+// a warp on 2 x 4 columns (cx, cy) and m = 0..3, the 32 lanes of every add hit 32
+// different banks: (16 cx + 19 cy + 4 m) mod 32 is distinct over them.
+__device__ __forceinline__ void home_quad(unsigned acc_s, const Record<float> (&r)[4], const bool (&has)[4], int cx,
+                                          int cy, int m, float sc0, float sc1, float sc2, float sc3)
 {
+    constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+    constexpr unsigned kMagicBits = 0x4B400000u;
+    float wx[4][4], wy[4][4], wz[4][4], q[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        int first;
+        bspline_weights<4, float>(has[j] ? r[j].u.x : 0.0f, wx[j], first);
+        bspline_weights<4, float>(has[j] ? r[j].u.y : 0.0f, wy[j], first);
+        bspline_weights<4, float>(has[j] ? r[j].u.z : 0.0f, wz[j], first);
+        q[j][0] = has[j] ? r[j].q.x * sc0 : 0.0f;
+        q[j][1] = has[j] ? r[j].q.y * sc1 : 0.0f;
+        q[j][2] = has[j] ? r[j].q.z * sc2 : 0.0f;
+        q[j][3] = has[j] ? r[j].q.w * sc3 : 0.0f;
+    }
+    // buffer index of node (cx - 1 + dx, cy - 1 + dy, 4m - 1 + i) is (cx + dx) PX + (cy + dy) PY + 4m + i.
+    // The 4 x 4 node columns are two rolled loops (a short body for the instruction
+    // cache); the weights of the current dx and dy are kept in slot 0 by rotating them.
+    unsigned base = acc_s + 4u * static_cast<unsigned>(cx * kHomePX + cy * kHomePY + 4 * m);
+#pragma unroll 1
+    for (int dx = 0; dx < 4; ++dx) {
+#pragma unroll 1
+        for (int dy = 0; dy < 4; ++dy) {
+            unsigned a[7][4];
+            static_for<7>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                constexpr unsigned cnt = static_cast<unsigned>((i < 3 ? i : 3) - (i > 3 ? i - 3 : 0) + 1);
+#pragma unroll
+                for (int f = 0; f < 4; ++f) a[i][f] = 0u - cnt * kMagicBits;
+            });
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float w01 = wx[j][0] * wy[j][0];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float ww = w01 * wz[j][k];
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) a[j + k][f] += __float_as_uint(fmaf(q[j][f], ww, kMagic));
+                }
+            }
+            const unsigned b = base + 4u * static_cast<unsigned>(dy * kHomePY);
+            static_for<7>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                red4<4 * i, 4 * kHomeField>(b, static_cast<int>(a[i][0]), static_cast<int>(a[i][1]),
+                                            static_cast<int>(a[i][2]), static_cast<int>(a[i][3]));
+            });
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {  // next dy in slot 0
+                const float t = wy[j][0];
+                wy[j][0] = wy[j][1], wy[j][1] = wy[j][2], wy[j][2] = wy[j][3], wy[j][3] = t;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {  // next dx in slot 0
+            const float t = wx[j][0];
+            wx[j][0] = wx[j][1], wx[j][1] = wx[j][2], wx[j][2] = wx[j][3], wx[j][3] = t;
+        }
+        base += 4u * kHomePX;
+    }
+}
+
+// A sorted particle of this tile (its cell read from the record); skipped if the record
+// does not lie in the tile. One copy for its three call sites (instruction cache).
+__device__ __noinline__ void home_listed(int *acc, const Record<float> *__restrict__ rec, uint32_t idx, int t0, int t1,
+                                         int t2, float sc0, float sc1, float sc2, float sc3)
+{
+    const Record<float> r = rec[idx];
     const int c = unpack_cell(r.u.w);
     const unsigned cx = static_cast<unsigned>((c & 1023) - t0), cy = static_cast<unsigned>(((c >> 10) & 1023) - t1),
                    cz = static_cast<unsigned>(((c >> 20) & 1023) - t2);
@@ -1485,59 +1559,68 @@ k_deposit_home(const Record<float> *__restrict__ rec, const uint32_t *__restrict
         int slot = wbeg + lane < wend ? find_slot<kHomeNT>(s_pre, wbeg + lane) : 0;
         for (uint32_t p = wbeg + lane; p < wend; p += 32) {
             while (p >= s_pre[slot + 1]) ++slot;
-            home_listed(acc, rec[s_beg[slot] + (p - s_pre[slot])], t0, t1, t2, sc0, sc1, sc2, sc3);
+            home_listed(acc, rec, s_beg[slot] + (p - s_pre[slot]), t0, t1, t2, sc0, sc1, sc2, sc3);
         }
     } else {
         uint32_t *q = s_cols + warp * kHomeQ;  // the column ranges are no longer needed
         __syncthreads();
         int qn = 0;  // warp-uniform queue length
-        const int xl = lane >> 4, cz = lane & 15;
-        constexpr int kBlocks = kHomeT * kHomeT / 2;
-        // loads run ahead: the offsets two blocks ahead, the first record one block ahead
-        auto cell_range = [&](int blk, uint32_t &b, uint32_t &e) {
+        const unsigned acc_s = static_cast<unsigned>(__cvta_generic_to_shared(acc));
+        // a block is 2 x 4 cell columns; lane (xl, yl, m) takes cells z = 4m .. 4m + 3
+        const int m = lane & 3, yl = (lane >> 2) & 3, xl = lane >> 4;
+        constexpr int kBlocks = (kHomeT / 2) * (kHomeT / 4);
+        auto cell_offsets = [&](int blk, uint32_t(&o)[5]) {  // the five offsets of the four cells
             if (blk >= kBlocks) {
-                b = e = 0;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) o[k] = 0;
                 return;
             }
-            const int cy = blk & 15, cx = 2 * (blk >> 4) + xl;
-            const int64_t key = (static_cast<int64_t>(t0 + cx) * ng + (t1 + cy)) * ng + (t2 + cz);
-            b = offsets[key];
-            e = offsets[key + 1];
+            const int cx = 2 * (blk >> 2) + xl, cy = 4 * (blk & 3) + yl;
+            const int64_t key = (static_cast<int64_t>(t0 + cx) * ng + (t1 + cy)) * ng + (t2 + 4 * m);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) o[k] = offsets[key + k];
         };
-        uint32_t beg1, end1, beg2, end2;
-        cell_range(warp, beg1, end1);
-        cell_range(warp + kHomeNW, beg2, end2);
-        Record<float> r1{};
-        if (end1 > beg1) r1 = rec[beg1];
+        uint32_t on[5];
+        cell_offsets(warp, on);  // loads run one block ahead
         for (int blk = warp; blk < kBlocks; blk += kHomeNW) {
-            const int cy = blk & 15, cx = 2 * (blk >> 4) + xl;
-            const uint32_t beg = beg1, end = end1;
-            const Record<float> r = r1;
-            beg1 = beg2, end1 = end2;
-            if (end1 > beg1) r1 = rec[beg1];
-            cell_range(blk + 2 * kHomeNW, beg2, end2);
-            if (end > beg) home_particle(acc, r, cx, cy, cz, sc0, sc1, sc2, sc3);
-            uint32_t next = beg + 1, extra = end > beg ? end - beg - 1 : 0u;
-            while (__any_sync(0xffffffffu, extra > 0u)) {
-                const bool has = extra > 0u;
-                const unsigned m = __ballot_sync(0xffffffffu, has);
-                if (has) {
-                    q[qn + __popc(m & ((1u << lane) - 1u))] = next;
-                    ++next;
-                    --extra;
-                }
-                qn += __popc(m);
-                __syncwarp();
-                if (qn >= 32) {
-                    home_listed(acc, rec[q[lane]], t0, t1, t2, sc0, sc1, sc2, sc3);
+            const int cx = 2 * (blk >> 2) + xl, cy = 4 * (blk & 3) + yl;
+            uint32_t o[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) o[k] = on[k];
+            cell_offsets(blk + kHomeNW, on);
+            Record<float> r[4];
+            bool has[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                has[k] = o[k + 1] > o[k];
+                r[k] = has[k] ? rec[o[k]] : Record<float>{};
+            }
+            home_quad(acc_s, r, has, cx, cy, m, sc0, sc1, sc2, sc3);
+            // second and later particles of the four cells: the per-warp queue, 32 at a time
+#pragma unroll 1
+            for (int k = 0; k < 4; ++k) {
+                uint32_t next = o[k] + 1, extra = has[k] ? o[k + 1] - o[k] - 1 : 0u;
+                while (__any_sync(0xffffffffu, extra > 0u)) {
+                    const bool more = extra > 0u;
+                    const unsigned mk = __ballot_sync(0xffffffffu, more);
+                    if (more) {
+                        q[qn + __popc(mk & ((1u << lane) - 1u))] = next;
+                        ++next;
+                        --extra;
+                    }
+                    qn += __popc(mk);
                     __syncwarp();
-                    if (lane < qn - 32) q[lane] = q[lane + 32];
-                    qn -= 32;
-                    __syncwarp();
+                    if (qn >= 32) {
+                        home_listed(acc, rec, q[lane], t0, t1, t2, sc0, sc1, sc2, sc3);
+                        __syncwarp();
+                        if (lane < qn - 32) q[lane] = q[lane + 32];
+                        qn -= 32;
+                        __syncwarp();
+                    }
                 }
             }
         }
-        if (lane < qn) home_listed(acc, rec[q[lane]], t0, t1, t2, sc0, sc1, sc2, sc3);
+        if (lane < qn) home_listed(acc, rec, q[lane], t0, t1, t2, sc0, sc1, sc2, sc3);
     }
     __syncthreads();
 #pragma unroll
