@@ -462,24 +462,27 @@ def main(argv=None):
         # copies its catalogue in and reads its spectra back. HostPipeline copies
         # catalogue i+1 while catalogue i is estimated (the link moves ~210 GB/s, about
         # the estimate's own pace at this size); pkmom_estimate_host (one call per step,
-        # copies not overlapped) is reported beside it.
+        # copies not overlapped) is reported beside it. The pipelined stream is 40
+        # catalogues long: its timed region includes the first copy, which nothing
+        # overlaps (about one step's time, spread over the stream).
         from paper_2005_06170_gb300.pipeline import HostPipeline
         hp = torch.from_numpy(cat["pos"]).pin_memory()
         hv = torch.from_numpy(cat["vel"]).pin_memory()
         hout = torch.empty((pkmom.NROWS, nbins), dtype=torch.float64).pin_memory()
         k_e = max(3, min(args.steps, 10))
+        k_pipe = 40
         pipe = HostPipeline(n_max=n, nbins_max=nbins, precision=p.precision)
         pipe.submit(hp, hv, p).result()  # warm-up: plans, tables, buffers
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         prev = None
-        for _ in range(k_e):
+        for _ in range(k_pipe):
             cur = pipe.submit(hp, hv, p)
             if prev is not None:
                 prev.result()
             prev = cur
         prev.result()
-        dt = (time.perf_counter() - t0) / k_e
+        dt = (time.perf_counter() - t0) / k_pipe
         pipe.close()
         hpn, hvn, hon = hp.numpy(), hv.numpy(), hout.numpy()
         ctx.estimate_host(hpn, hvn, p, out=hon, stream=stream)
@@ -488,9 +491,10 @@ def main(argv=None):
             ctx.estimate_host(hpn, hvn, p, out=hon, stream=stream)
         dt1 = (time.perf_counter() - t1) / k_e
         line["e2e"] = {"value": n / dt, "unit": "particles/s", "h2d_bytes_per_step": int(hp.nbytes + hv.nbytes),
-                       "d2h_bytes_per_step": int(hout.nbytes), "ms_per_step": dt * 1e3, "steps": k_e,
+                       "d2h_bytes_per_step": int(hout.nbytes), "ms_per_step": dt * 1e3, "steps": k_pipe,
                        "api": "HostPipeline (copy of step i+1 overlaps the estimate of step i)",
-                       "single_call": {"value": n / dt1, "ms_per_step": dt1 * 1e3, "api": "pkmom_estimate_host"}}
+                       "single_call": {"value": n / dt1, "ms_per_step": dt1 * 1e3, "steps": k_e,
+                                       "api": "pkmom_estimate_host"}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cat, args.workload)
     ctx.close()
