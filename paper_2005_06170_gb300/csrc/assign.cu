@@ -1004,6 +1004,7 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
     const int ty = tile % nty;
     const int tx = tile / nty;
     const int t0 = tx * T0, t1 = ty * T1, t2 = tz * T2;
+    const float qm = threadIdx.x < 4 ? __uint_as_float(qmax_bits[threadIdx.x]) : 0.0f;  // used after the list
     for (int k = threadIdx.x; k < TNP; k += NT) reinterpret_cast<int4 *>(acc)[k] = make_int4(0, 0, 0, 0);
     if (threadIdx.x == 0) s_rowmax = 0;
     const uint32_t total = build_ranges<C>(offsets, ng, sshift, t0, t1, t2, T2, s_beg, s_pre);
@@ -1068,7 +1069,7 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
     __syncthreads();
     if (threadIdx.x < 4) {
         const int f = threadIdx.x;
-        const float m = __uint_as_float(qmax_bits[f]);  // max |q_f| over the catalogue
+        const float m = qm;  // max |q_f| over the catalogue, loaded at the start
         const float w3 = kMaxW3<M, BLR> * 1.0001f;
         const float reach = fminf(static_cast<float>(M * M) * static_cast<float>(s_rowmax), static_cast<float>(total));
         tile_scales(w3 * reach * m, w3 * m, dense, s_scale[f], s_fine[f], s_shift[f]);
@@ -1208,13 +1209,29 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
     }
     __syncthreads();
     const float inv[4] = {1.0f / sc0, 1.0f / sc1, 1.0f / sc2, 1.0f / sc3};  // exact: powers of two
-    for (int k = threadIdx.x; k < C::TN; k += NT) {
-        const int l2 = k % T2, l01 = k / T2;
-        const int l1 = l01 % T1, l0 = l01 / T1;
-        const int64_t gi = (static_cast<int64_t>(t0 + l0) * ng + (t1 + l1)) * (ng + 2) + t2 + l2;
-        const int ai = l0 * PX + l1 * RW + l2;
+    if ((reinterpret_cast<uintptr_t>(grids) & 7u) == 0) {
+        // two z-adjacent cells per thread, one 8-byte store per field (ng, the row pitch
+        // ng + 2, t2 and the even l2 keep the pair aligned)
+        for (int k = threadIdx.x; k < C::TN / 2; k += NT) {
+            const int l2 = 2 * (k % (T2 / 2)), l01 = k / (T2 / 2);
+            const int l1 = l01 % T1, l0 = l01 / T1;
+            const int64_t gi = (static_cast<int64_t>(t0 + l0) * ng + (t1 + l1)) * (ng + 2) + t2 + l2;
+            const int ai = l0 * PX + l1 * RW + l2;
 #pragma unroll
-        for (int f = 0; f < 4; ++f) grids[f * grid_elems + gi] = static_cast<float>(acc[f * TNP + ai]) * inv[f];
+            for (int f = 0; f < 4; ++f)
+                *reinterpret_cast<float2 *>(grids + f * grid_elems + gi) =
+                    make_float2(static_cast<float>(acc[f * TNP + ai]) * inv[f],
+                                static_cast<float>(acc[f * TNP + ai + 1]) * inv[f]);
+        }
+    } else {
+        for (int k = threadIdx.x; k < C::TN; k += NT) {
+            const int l2 = k % T2, l01 = k / T2;
+            const int l1 = l01 % T1, l0 = l01 / T1;
+            const int64_t gi = (static_cast<int64_t>(t0 + l0) * ng + (t1 + l1)) * (ng + 2) + t2 + l2;
+            const int ai = l0 * PX + l1 * RW + l2;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) grids[f * grid_elems + gi] = static_cast<float>(acc[f * TNP + ai]) * inv[f];
+        }
     }
 }
 
@@ -1470,6 +1487,7 @@ k_deposit_home(const Record<float> *__restrict__ rec, const uint32_t *__restrict
     const int nt = ng / kHomeT;
     const int tz = blockIdx.x % nt, ty = (blockIdx.x / nt) % nt, tx = blockIdx.x / (nt * nt);
     const int t0 = tx * kHomeT, t1 = ty * kHomeT, t2 = tz * kHomeT;
+    const float qm = threadIdx.x < 4 ? __uint_as_float(qmax_bits[threadIdx.x]) : 0.0f;  // used after the scan
     {
         int4 *a4 = reinterpret_cast<int4 *>(acc);
         for (int k = threadIdx.x; k < kHomeField; k += kHomeNT) a4[k] = make_int4(0, 0, 0, 0);  // 4 fields / 4 ints
@@ -1503,7 +1521,7 @@ k_deposit_home(const Record<float> *__restrict__ rec, const uint32_t *__restrict
     const bool sparse = !dense && total < kCells / 4u;
     if (threadIdx.x < 4) {
         const int f = threadIdx.x;
-        const float m = __uint_as_float(qmax_bits[f]);  // max |q_f| over the catalogue
+        const float m = qm;  // max |q_f| over the catalogue, loaded at the start
         const float w3 = kMaxWeight3<4> * 1.0001f;
         // a node receives from 4 consecutive cells of at most 4 x 4 columns of the tile
         const float reach = fminf(16.0f * static_cast<float>(s_rowmax), static_cast<float>(total));
