@@ -436,7 +436,7 @@ def main(argv=None):
     home = home and not args.bl_radius
     deposit_kernels = "k_deposit_home + k_home_fixup" if home else ("k_deposit_fx" if prec == "f32" else "k_deposit")
     traffic = None if args.bl_radius else MEASURED_TRAFFIC.get((args.workload, dom))
-    roof = {"kernel": {"deposit": deposit_kernels, "bin": "k_bin_shells + k_reduce_items", "hist": "k_hist_moments",
+    roof = {"kernel": {"deposit": deposit_kernels, "bin": "k_bin_shells + k_reduce_items", "hist": "k_hist",
                        "scatter": "k_scatter", "scan": "k_scan_*", "final": "k_finalize"}[dom],
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None,
