@@ -45,6 +45,9 @@ WORKLOADS = {
     "zeldovich512_ng1024": ("Zel'dovich 512^3 particles, L=1500 Mpc/h, 1024^3 FP32 grid, BL3, 128 shells, "
                             "with and without bulk flow", dict(kind="zeldovich", n_side=512, L=1500.0, seed=1002),
                             1024, 128, "f32"),
+    "poisson830k_ng384": ("830,584 Poisson particles, L=900 Mpc/h, 384^3 FP32 grid, BL3, 128 shells (0.015 particle "
+                          "per cell, as in the sparsest catalogues of the batch)",
+                          dict(kind="poisson", n=830584, L=900.0, seed=5), 384, 128, "f32"),
 }
 DEFAULT = "zeldovich256_ng256"
 # DRAM bytes (read + write) per launch of the dominant stage's kernels, from one ncu
