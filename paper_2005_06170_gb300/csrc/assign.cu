@@ -1274,6 +1274,22 @@ static_assert(kHomePX % 32 == 16 && kHomePX >= kHomeB * kHomeB, "x-adjacent cell
 static_assert(kHomeNT == kHomeT * kHomeT, "one thread per cell column");
 static_assert(kHomeNW * kHomeQ <= 2 * kHomeNT + 1, "queues share the column-range arrays");
 
+// Banks of the first stencil node of the 32 lanes of a four-cells-per-lane block (2 x 4
+// columns, lane (x, y, m) at cells z = 4m .. 4m + 3): all different, so that every add
+// of home_quad is one wavefront.
+constexpr bool home_quad_banks_distinct()
+{
+    unsigned seen = 0;
+    for (int lane = 0; lane < 32; ++lane) {
+        const int m = lane & 3, y = (lane >> 2) & 3, x = lane >> 4;
+        const unsigned bit = 1u << ((x * kHomePX + y * kHomePY + 4 * m) & 31);
+        if (seen & bit) return false;
+        seen |= bit;
+    }
+    return true;
+}
+static_assert(home_quad_banks_distinct(), "the 32 lanes of a home_quad add must hit 32 banks");
+
 // Halo index of buffer node (bx, by, bz), at least one coordinate in {0, 17, 18}:
 // first the three x planes (19 x 19 each), then the y planes of the inner x range
 // (16 x 19), then the z planes of the inner x, y range (16 x 16).
