@@ -178,6 +178,21 @@ def run_reference(args):
     return 0
 
 
+def replica_throughput(elapsed_ms: float, units: int, steps: int, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas: every rank processed `units` per
+    step for `steps` steps, and the job took the slowest rank's time (a MAX all-reduce
+    over the process group, on `device`: a CUDA device for NCCL, the CPU for gloo).
+    Returns (that time in ms, units per second over all ranks)."""
+    world = 1
+    if dist is not None:
+        import torch
+        t = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        world = dist.get_world_size()
+    return elapsed_ms, world * units * steps / (elapsed_ms * 1e-3)
+
+
 def _clock_id(torch, dev):
     try:
         return "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
@@ -403,13 +418,8 @@ def main(argv=None):
         stages = ctx.timing_read()
         ctx.timing(False)
         ctx.sync(stream)
-    elapsed_ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms, value = replica_throughput(e0.elapsed_time(e1), n, args.steps, dist, dev)
     ms_step = elapsed_ms / args.steps
-    value = world * n * args.steps / (elapsed_ms * 1e-3)
     cells_s = world * ng ** 3 * args.steps / (elapsed_ms * 1e-3)
 
     # roofline of the dominant own kernel, from the stage events of the timed region
