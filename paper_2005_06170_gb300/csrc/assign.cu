@@ -1245,11 +1245,13 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
 // each neighbour's halo to the owned nodes it overlaps, in a fixed order (so the grids
 // do not depend on scheduling).
 //
-// Lane mapping: a warp takes a block of 2 x 16 cells (two x-adjacent cells, 16 z cells)
-// and each lane deposits the first particle of its cell. The buffer's x pitch is 16
-// modulo 32 banks and its z pitch 1, so for every stencil offset the 32 lanes hit 32
-// different banks: the shared atomics of a block take one wavefront each. Particles
-// beyond the first of a cell go to a per-warp queue and are deposited 32 at a time.
+// Lane mapping: a warp takes a block of 2 x 4 cell columns; lane (x, y, m) takes the
+// first particles of cells z = 4m .. 4m + 3 of its column and sums their contributions
+// to each node column's 7 z nodes in registers before adding them (home_quad). The
+// buffer's x pitch is 16 modulo 32 banks, its y pitch 19 and its z pitch 1, so the 32
+// lanes of every add hit 32 different banks (checked at compile time below): one
+// wavefront each. Particles beyond the first of a cell go to a per-warp queue and are
+// deposited 32 at a time, one per lane.
 // Tiles with more than two particles per cell, or 32 in some four consecutive cells of a
 // column, take the cell-block path: one warp per cell, each contribution rounded at the
 // fine scale (largest contribution < 2^22) and summed exactly, in 64-bit shared
