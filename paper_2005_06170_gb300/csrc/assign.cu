@@ -438,7 +438,7 @@ k_scatter(const T *__restrict__ x, const T *__restrict__ y, const T *__restrict_
 // Offset from floor(u) of the first of the M nodes the order-M B-spline reaches for a
 // particle at offset t in its cell (the convention of bspline_weights below).
 template <int M, typename T>
-__device__ __forceinline__ int bspline_first(T t)
+__host__ __device__ constexpr int bspline_first(T t)
 {
     if constexpr (M == 5) return t >= T(0.5) ? -1 : -2;
     else if constexpr (M == 4) return -1;
@@ -880,6 +880,32 @@ struct FxLayout {
         return size_t(FRONT + 4 * TNP + (list_cap > BACK ? list_cap : BACK)) * sizeof(int);
     }
 };
+
+// Every node the listed path adds to (weights of nodes outside the tile zero) lies in the
+// padded allocation: node coordinates run from -HL + first(0) to (T + HR - 1) + first(1/2)
+// + M - 1 on each axis (first is smallest at t = 0 and largest from t = 1/2 on).
+template <int M, int T0, int T1, int T2>
+constexpr bool fx_pads_cover()
+{
+    using Lay = FxLayout<T0, T1, T2>;
+    constexpr int HL = (M % 2 == 0) ? M / 2 : (M + 1) / 2;
+    constexpr int HR = (M % 2 == 0) ? M / 2 - 1 : (M - 1) / 2;
+    constexpr int lo = -HL + bspline_first<M, float>(0.0f);
+    constexpr int up = HR - 1 + bspline_first<M, float>(0.5f) + M - 1;  // highest coordinate - T
+    constexpr long min_lin = static_cast<long>(lo) * (Lay::PX + Lay::RW + 1);
+    constexpr long max_lin = static_cast<long>(T0 + up) * Lay::PX + static_cast<long>(T1 + up) * Lay::RW + (T2 + up) +
+                             3L * Lay::TNP;
+    return min_lin >= -Lay::FRONT && max_lin < 4L * Lay::TNP + Lay::BACK;
+}
+template <int T0, int T1, int T2>
+constexpr bool fx_pads_cover_orders()
+{
+    return fx_pads_cover<1, T0, T1, T2>() && fx_pads_cover<2, T0, T1, T2>() && fx_pads_cover<3, T0, T1, T2>() &&
+           fx_pads_cover<4, T0, T1, T2>() && fx_pads_cover<5, T0, T1, T2>();
+}
+static_assert(fx_pads_cover_orders<16, 16, 16>() && fx_pads_cover_orders<16, 16, 32>() &&
+                  fx_pads_cover_orders<8, 8, 32>() && fx_pads_cover_orders<8, 8, 8>(),
+              "the padding of the gather accumulator must cover every node the listed path adds to");
 
 // Four shared-memory adds at byte offsets OFF + f * FS (f = 0..3) from addr (the offsets
 // are immediates).
