@@ -1317,6 +1317,10 @@ constexpr bool home_quad_banks_distinct()
     return true;
 }
 static_assert(home_quad_banks_distinct(), "the 32 lanes of a home_quad add must hit 32 banks");
+// home_quad's largest buffer index on each axis: cell 15 + node offset 3 in x and y,
+// z = 4 * 3 + 6 (seven z nodes from the lane's first cell); all inside the 19-node edge
+static_assert(kHomeT - 1 + 3 < kHomeB && 4 * 3 + 6 < kHomeB && kHomeT % 4 == 0 && kHomeT / 4 == 4,
+              "home_quad's nodes must lie in the node buffer");
 
 // Halo index of buffer node (bx, by, bz), at least one coordinate in {0, 17, 18}:
 // first the three x planes (19 x 19 each), then the y planes of the inner x range
