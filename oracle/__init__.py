@@ -11,8 +11,12 @@ Modules:
     deposit.c  - FP64 B-spline assignment of particles to the grid (plain C)
     estimator  - moments, assignment, FFT, shot noise, deconvolution, binning,
                  bulk-flow variant (Secs. 2 and 3 of the paper)
-    direct     - brute-force references used only to pin the above (direct
-                 real-space BL deposit, brute-force DFT, full-sphere binning)
+    direct     - the BL function deposited in real space (whole, or truncated to a
+                 radius: the oracle of the direct truncated deposit), and brute-force
+                 references that pin the above (brute-force DFT, full-sphere binning)
+    mu         - the spectra binned in (|k|, mu) about the bulk flow or a direction
+                 (Sec. 2.2 and Sec. 3.2: the mu-dependent shot noise and the imaginary
+                 cross spectrum that shell averages cancel)
 
 Parity unpinned: nothing. Every function above is checked in tests/test_oracle_*.py
 against closed forms, brute force or exact identities.
