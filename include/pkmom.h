@@ -33,7 +33,8 @@
  *
  * Ownership: every buffer passed in is owned by the caller. A context owns its
  * cuFFT plans, its cached per-grid tables and, for pkmom_estimate and
- * pkmom_estimate_host only, the grids and scratch it allocates on first use.
+ * pkmom_estimate_host(_async) only, the grids, scratch and staging it allocates on
+ * first use.
  * All calls are asynchronous on the given CUDA stream (a cudaStream_t passed as
  * void*; NULL = legacy default stream) unless stated. Argument errors are
  * returned synchronously; a device-side error (a non-finite position) is latched
@@ -112,7 +113,7 @@ enum {
  * in elements (1 for separate arrays, 3 for interleaved (n,3) position and
  * velocity arrays). mass may be NULL (unit masses). dtype is PKMOM_F32 or
  * PKMOM_F64 and must equal the precision in pkmom_params. Device pointers for
- * every call except pkmom_estimate_host (host pointers there). */
+ * every call except pkmom_estimate_host(_async) (host pointers there). */
 typedef struct {
     int64_t n;
     const void *x, *y, *z, *vx, *vy, *vz;
@@ -217,9 +218,31 @@ pkmom_status pkmom_estimate(pkmom_ctx *ctx, const pkmom_catalog *cat, const pkmo
 pkmom_status pkmom_estimate_host(pkmom_ctx *ctx, const pkmom_catalog *cat_host, const pkmom_params *p,
                                  double *out_host, void *stream);
 
-/* Step 4 like pkmom_spectra, for callers that cannot allocate device memory (for
- * example code replayed inside a CUDA graph, or a host application that owns a fixed
- * device pool and forbids allocator calls). This one entry point has no counterpart
+/* Steps 1-4 on a HOST catalogue without waiting for them: the pipelined form of
+ * pkmom_estimate_host for a stream of catalogues. The catalogue is copied (one
+ * cudaMemcpyAsync per array) on a copy stream the context owns, into the one of two
+ * context-owned device staging slots that the estimate before the previous one has
+ * finished reading; the estimate runs on `stream` once its copy has landed, and its
+ * PKMOM_NROWS * nbins result is copied to out_host on `stream`. So the copy of catalogue
+ * i+1 overlaps the estimate of catalogue i. Returns at once with *ticket, the call's
+ * sequence number on this context; pkmom_wait(ctx, ticket) waits for the result.
+ * Until then the caller keeps cat_host's arrays unchanged and out_host alive. Host
+ * arrays must be pinned (page-locked) for the copies to overlap the compute; pageable
+ * memory gives correct results with the copies serialised. A context has one staging
+ * pair and one set of grids: use one `stream` per context for these calls. */
+pkmom_status pkmom_estimate_host_async(pkmom_ctx *ctx, const pkmom_catalog *cat_host, const pkmom_params *p,
+                                       double *out_host, void *stream, int64_t *ticket);
+
+/* Waits until the result of the pkmom_estimate_host_async call numbered `ticket` is in
+ * its out_host array (and every earlier call's result is in its own), then returns any
+ * device-side data error latched by the estimates finished so far (PKMOM_EDATA).
+ * PKMOM_EINVAL for a ticket this context has not issued. */
+pkmom_status pkmom_wait(pkmom_ctx *ctx, int64_t ticket);
+
+/* Step 4 like pkmom_spectra, for callers that cannot allocate device memory: a host
+ * application that owns a fixed device pool and forbids allocator calls, or a plug-in
+ * that runs inside another program and must not grow its footprint or call into its
+ * allocator. This one entry point has no counterpart
  * in the paper: it exists only so that such callers can run the binning step.
  * It allocates nothing: its scratch (shell table, window tables, partial and shell
  * sums) is one file-scope device array of 4 MiB, held by every GPU that loads the
@@ -250,6 +273,12 @@ pkmom_status pkmom_timing_read(pkmom_ctx *ctx, double ms[PKMOM_NSTAGES], int64_t
 
 /* Number of kernels this context has launched (its own kernels; cuFFT's not counted). */
 int64_t pkmom_kernel_launches(const pkmom_ctx *ctx);
+
+/* Device bytes this context holds now: the workspaces of its cached cuFFT plans, its
+ * cached per-grid tables and the buffers that pkmom_estimate, pkmom_estimate_host(_async)
+ * and pkmom_spectra_mu own. A caller that budgets device memory (the serving loop)
+ * charges these beside the buffers it passes in. */
+size_t pkmom_context_bytes(const pkmom_ctx *ctx);
 
 /* Tuning knobs of the assignment (used by the autotuner): deposit tile shape id
  * (0: 16x16x16, 1: 16x16x32, 2: 8x8x32, 3: 8x8x8 for FP32 grids; 4: 8x8x16, 5: 16^3,

@@ -17,7 +17,7 @@ The steps follow the paper in its own order:
 7. the same with the bulk flow removed, v' = v - v_b, p' = p - (1+delta) v_b
    (Sec. 3.1), which on the grid is F_p' = F_p - v_b F_delta.
 
-Conventions (readings of the paper, all listed in the design doc):
+Conventions (readings of the paper where it is silent or ambiguous):
 * Positions: grid coordinate u = x * (ng / L). For an FP32 catalogue u is formed in
   FP32 (u = fl32(x * fl32(ng/L))), the precision in which the GPU takes the
   cell decision; for an FP64 catalogue in FP64. Everything after that is FP64.
@@ -86,9 +86,17 @@ def assign(pos, vel, mass, *, L: float, ng: int, order: int = 4) -> np.ndarray:
 
 
 def fft_grids(grids: np.ndarray, workers: int = -1) -> np.ndarray:
-    """R2C FFT (e^{-ikr}, unnormalised) of each grid over its three axes."""
+    """R2C FFT (e^{-ikr}, unnormalised) of each grid over its three axes, one grid at a
+    time into one output array (so that a 1024^3 run holds one transform beside it)."""
     import scipy.fft
-    return np.stack([scipy.fft.rfftn(g, workers=workers) for g in grids])
+    out = None
+    for f, g in enumerate(grids):
+        t = scipy.fft.rfftn(g, workers=workers)
+        if out is None:
+            out = np.empty((len(grids),) + t.shape, dtype=t.dtype)
+        out[f] = t
+        del t
+    return out
 
 
 def signed_freq(ng: int) -> np.ndarray:
@@ -120,13 +128,14 @@ def spectra_from_fourier(F: np.ndarray, mom: dict, *, L: float, ng: int, order: 
                          nbins: int, kmin_kf: float = 1.0, kmax_kf: float | None = None,
                          theta_scale: float = 1.0, subtract_shot_noise: bool = True,
                          theta_sn: str = "tensor", bulk: bool = True,
-                         per_mode: bool = False, bl_assigned: bool = False) -> dict:
+                         per_mode: bool = False, bl_assigned: bool = False, slabs=None) -> dict:
     """Steps 4-7 on the Fourier transforms F[4] of the B-spline-deposited grids.
 
     bl_assigned: F holds grids already assigned with the BL function itself (the direct
     real-space deposit), so the Fourier-space factor prod Sigma^{-1/2} is not applied.
     Returns shell averages. With per_mode=True also returns the per-mode arrays
-    (only sensible for small grids).
+    (only sensible for small grids). slabs: the first-axis indices to visit (default
+    all); a subset gives partial sums, used only to time a bounded sample.
     """
     umin = float(kmin_kf)
     umax = float(ng // 2 if kmax_kf is None else kmax_kf)
@@ -150,7 +159,7 @@ def spectra_from_fourier(F: np.ndarray, mom: dict, *, L: float, ng: int, order: 
     modes = {} if per_mode else None
     vb = mom["vb"]
     variants = [("", mom["Q"])] + ([("_b", mom["Qp"])] if bulk else [])
-    for i0 in range(ng):
+    for i0 in (range(ng) if slabs is None else slabs):
         n1 = nfull[:, None]
         n2 = nhalf[None, :]
         n0 = nfull[i0]

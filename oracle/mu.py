@@ -59,6 +59,9 @@ def mu_bin32(n0, n1, n2, e, nmu: int) -> np.ndarray:
     with np.errstate(invalid="ignore", divide="ignore"):
         mu = (d / r).astype(f)
     t = ((mu + f(1)).astype(f) * f(nmu / 2)).astype(f)
+    # the k = 0 mode has no direction (0/0); callers leave it out, so give it bin 0
+    # rather than cast a NaN to an integer
+    t = np.where(nn > 0, t, f(0))
     m = np.floor(t).astype(np.int64)
     return np.clip(m, 0, nmu - 1)
 

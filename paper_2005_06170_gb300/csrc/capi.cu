@@ -18,6 +18,7 @@ using namespace pkmom;
 struct PlanEntry {
     int ng, prec;
     cufftHandle h;
+    size_t work;  // bytes of the workspace cuFFT allocated for the plan
 };
 
 struct TimedEvent {
@@ -43,6 +44,16 @@ struct pkmom_ctx {
     size_t out_bytes = 0;
     void *staging = nullptr;
     size_t staging_bytes = 0;
+    // pkmom_estimate_host_async: two staging slots filled on a copy stream, the events
+    // that order them against the estimates, and a ring of completion events by ticket
+    static constexpr int kRing = 8;
+    void *aslot[2] = {nullptr, nullptr};
+    size_t aslot_bytes[2] = {0, 0};
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t slot_copied[2] = {nullptr, nullptr};
+    cudaEvent_t slot_free[2] = {nullptr, nullptr};
+    cudaEvent_t done[kRing] = {};
+    int64_t next_ticket = 0;
     // work arrays of pkmom_spectra_mu
     void *mu_partials = nullptr;
     size_t mu_partials_bytes = 0;
@@ -263,7 +274,7 @@ pkmom_status get_plan(pkmom_ctx *ctx, int ng, int prec, cufftHandle *out)
         std::snprintf(buf, sizeof buf, "cufftPlanMany(ng=%d) failed with code %d", ng, int(r));
         return fail(ctx, r == CUFFT_ALLOC_FAILED ? PKMOM_ENOMEM : PKMOM_ECUFFT, buf);
     }
-    ctx->plans.push_back({ng, prec, h});
+    ctx->plans.push_back({ng, prec, h, work});
     *out = h;
     return PKMOM_OK;
 }
@@ -302,6 +313,71 @@ pkmom_status ensure(pkmom_ctx *ctx, void **buf, size_t *have, size_t want, const
         return cuda_fail(ctx, e, what);
     }
     *have = want;
+    return PKMOM_OK;
+}
+
+// Arguments of a host-catalogue estimate (pkmom_estimate_host and its async form).
+pkmom_status check_host_request(pkmom_ctx *ctx, const pkmom_catalog *cat, const pkmom_params *p, const double *out)
+{
+    pkmom_status s;
+    if ((s = check_params(ctx, p)) != PKMOM_OK) return s;
+    if ((s = check_catalog(ctx, cat, p)) != PKMOM_OK) return s;
+    if (!out) return fail(ctx, PKMOM_EINVAL, "null output");
+    const size_t elem = p->precision == PKMOM_F64 ? 8 : 4;
+    const char *bx = static_cast<const char *>(cat->x);
+    const char *bv = static_cast<const char *>(cat->vx);
+    const bool pos_il = cat->stride == 3 && static_cast<const char *>(cat->y) == bx + elem &&
+                        static_cast<const char *>(cat->z) == bx + 2 * elem;
+    const bool vel_il = cat->stride == 3 && static_cast<const char *>(cat->vy) == bv + elem &&
+                        static_cast<const char *>(cat->vz) == bv + 2 * elem;
+    if (cat->stride != 1 && !(pos_il && vel_il))
+        return fail(ctx, PKMOM_EUNSUPPORTED, "host catalogues must be separate arrays or interleaved (n,3) arrays");
+    return PKMOM_OK;
+}
+
+// Device staging of a host catalogue: seven blocks of n elements (x, y, z, vx, vy, vz, m).
+size_t staging_bytes(int64_t n, size_t elem) { return 7 * align_up(size_t(n) * elem); }
+
+// Copies a host catalogue into the staging area stg on stream st (one cudaMemcpyAsync per
+// array; interleaved (n,3) arrays as one block each) and describes the device copy.
+pkmom_status stage_catalog(pkmom_ctx *ctx, const pkmom_catalog &cat, size_t elem, char *stg, cudaStream_t st,
+                           pkmom_catalog *dcat)
+{
+    const int64_t n = cat.n;
+    const size_t block = align_up(size_t(n) * elem);
+    *dcat = cat;
+    if (cat.stride == 3) {
+        PK_CUDA(cudaMemcpyAsync(stg, cat.x, 3 * size_t(n) * elem, cudaMemcpyHostToDevice, st), "copy positions");
+        PK_CUDA(cudaMemcpyAsync(stg + 3 * block, cat.vx, 3 * size_t(n) * elem, cudaMemcpyHostToDevice, st),
+                "copy velocities");
+        dcat->x = stg, dcat->y = stg + elem, dcat->z = stg + 2 * elem;
+        dcat->vx = stg + 3 * block, dcat->vy = stg + 3 * block + elem, dcat->vz = stg + 3 * block + 2 * elem;
+    } else {
+        const void *src[6] = {cat.x, cat.y, cat.z, cat.vx, cat.vy, cat.vz};
+        const void **dst[6] = {&dcat->x, &dcat->y, &dcat->z, &dcat->vx, &dcat->vy, &dcat->vz};
+        for (int a = 0; a < 6; ++a) {
+            PK_CUDA(cudaMemcpyAsync(stg + a * block, src[a], size_t(n) * elem, cudaMemcpyHostToDevice, st),
+                    "copy catalogue");
+            *dst[a] = stg + a * block;
+        }
+    }
+    if (cat.mass) {
+        PK_CUDA(cudaMemcpyAsync(stg + 6 * block, cat.mass, size_t(n) * elem, cudaMemcpyHostToDevice, st),
+                "copy masses");
+        dcat->mass = stg + 6 * block;
+    }
+    return PKMOM_OK;
+}
+
+// Returns (and clears) a device-side data error latched by the context's kernels.
+pkmom_status check_error_word(pkmom_ctx *ctx)
+{
+    int flag = 0;
+    PK_CUDA(cudaMemcpy(&flag, ctx->d_err, sizeof flag, cudaMemcpyDeviceToHost), "read error word");
+    if (flag) {
+        PK_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)), "clear error word");
+        return fail(ctx, PKMOM_EDATA, "catalogue held non-finite or out-of-range positions (|x ng/L| >= 2^30)");
+    }
     return PKMOM_OK;
 }
 
@@ -378,6 +454,14 @@ pkmom_status pkmom_destroy(pkmom_ctx *ctx)
     cudaFree(ctx->moments);
     cudaFree(ctx->out_dev);
     cudaFree(ctx->staging);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(ctx->aslot[k]);
+        if (ctx->slot_copied[k]) cudaEventDestroy(ctx->slot_copied[k]);
+        if (ctx->slot_free[k]) cudaEventDestroy(ctx->slot_free[k]);
+    }
+    for (auto e : ctx->done)
+        if (e) cudaEventDestroy(e);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     cudaFree(ctx->mu_partials);
     cudaFree(ctx->mu_sums);
     cudaFree(ctx->d_err);
@@ -550,53 +634,92 @@ pkmom_status pkmom_estimate_host(pkmom_ctx *ctx, const pkmom_catalog *cat, const
 {
     if (!ctx) return PKMOM_EINVAL;
     pkmom_status s;
-    if ((s = check_params(ctx, p)) != PKMOM_OK) return s;
-    if ((s = check_catalog(ctx, cat, p)) != PKMOM_OK) return s;
-    if (!out_host) return fail(ctx, PKMOM_EINVAL, "null output");
+    if ((s = check_host_request(ctx, cat, p, out_host)) != PKMOM_OK) return s;
     PK_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
     const size_t elem = p->precision == PKMOM_F64 ? 8 : 4;
-    const int64_t n = cat->n;
-    // interleaved (n,3) arrays are copied as one block each; separate arrays one by one
-    const char *bx = static_cast<const char *>(cat->x);
-    const char *bv = static_cast<const char *>(cat->vx);
-    const bool pos_il = cat->stride == 3 && static_cast<const char *>(cat->y) == bx + elem &&
-                        static_cast<const char *>(cat->z) == bx + 2 * elem;
-    const bool vel_il = cat->stride == 3 && static_cast<const char *>(cat->vy) == bv + elem &&
-                        static_cast<const char *>(cat->vz) == bv + 2 * elem;
-    if (cat->stride != 1 && !(pos_il && vel_il))
-        return fail(ctx, PKMOM_EUNSUPPORTED, "host catalogues must be separate arrays or interleaved (n,3) arrays");
-    const size_t block = align_up(size_t(n) * elem);
-    const size_t want = 7 * block;
-    if ((s = ensure(ctx, &ctx->staging, &ctx->staging_bytes, want, "staging")) != PKMOM_OK) return s;
+    if ((s = ensure(ctx, &ctx->staging, &ctx->staging_bytes, staging_bytes(cat->n, elem), "staging")) != PKMOM_OK)
+        return s;
     const size_t out_bytes = size_t(PKMOM_NROWS) * p->nbins * sizeof(double);
     if ((s = ensure(ctx, reinterpret_cast<void **>(&ctx->out_dev), &ctx->out_bytes, out_bytes, "output")) != PKMOM_OK)
         return s;
     cudaStream_t st = as_stream(stream);
-    char *stg = static_cast<char *>(ctx->staging);
-    pkmom_catalog dcat = *cat;
-    if (cat->stride == 3) {
-        PK_CUDA(cudaMemcpyAsync(stg, cat->x, 3 * size_t(n) * elem, cudaMemcpyHostToDevice, st), "copy positions");
-        PK_CUDA(cudaMemcpyAsync(stg + 3 * block, cat->vx, 3 * size_t(n) * elem, cudaMemcpyHostToDevice, st),
-                "copy velocities");
-        dcat.x = stg, dcat.y = stg + elem, dcat.z = stg + 2 * elem;
-        dcat.vx = stg + 3 * block, dcat.vy = stg + 3 * block + elem, dcat.vz = stg + 3 * block + 2 * elem;
-    } else {
-        const void *src[6] = {cat->x, cat->y, cat->z, cat->vx, cat->vy, cat->vz};
-        const void **dst[6] = {&dcat.x, &dcat.y, &dcat.z, &dcat.vx, &dcat.vy, &dcat.vz};
-        for (int a = 0; a < 6; ++a) {
-            PK_CUDA(cudaMemcpyAsync(stg + a * block, src[a], size_t(n) * elem, cudaMemcpyHostToDevice, st),
-                    "copy catalogue");
-            *dst[a] = stg + a * block;
-        }
-    }
-    if (cat->mass) {
-        PK_CUDA(cudaMemcpyAsync(stg + 6 * block, cat->mass, size_t(n) * elem, cudaMemcpyHostToDevice, st),
-                "copy masses");
-        dcat.mass = stg + 6 * block;
-    }
+    pkmom_catalog dcat;
+    if ((s = stage_catalog(ctx, *cat, elem, static_cast<char *>(ctx->staging), st, &dcat)) != PKMOM_OK) return s;
     if ((s = pkmom_estimate(ctx, &dcat, p, ctx->out_dev, stream)) != PKMOM_OK) return s;
     PK_CUDA(cudaMemcpyAsync(out_host, ctx->out_dev, out_bytes, cudaMemcpyDeviceToHost, st), "copy result");
     return pkmom_sync(ctx, stream);
+}
+
+pkmom_status pkmom_estimate_host_async(pkmom_ctx *ctx, const pkmom_catalog *cat, const pkmom_params *p,
+                                       double *out_host, void *stream, int64_t *ticket)
+{
+    if (!ctx) return PKMOM_EINVAL;
+    pkmom_status s;
+    if ((s = check_host_request(ctx, cat, p, out_host)) != PKMOM_OK) return s;
+    if (!ticket) return fail(ctx, PKMOM_EINVAL, "null ticket");
+    PK_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const size_t elem = p->precision == PKMOM_F64 ? 8 : 4;
+    cudaStream_t st = as_stream(stream);
+    if (!ctx->copy_stream) {
+        PK_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking), "copy stream");
+        for (int k = 0; k < 2; ++k) {
+            PK_CUDA(cudaEventCreateWithFlags(&ctx->slot_copied[k], cudaEventDisableTiming), "slot event");
+            PK_CUDA(cudaEventCreateWithFlags(&ctx->slot_free[k], cudaEventDisableTiming), "slot event");
+            PK_CUDA(cudaEventRecord(ctx->slot_free[k], ctx->copy_stream), "slot event");
+        }
+        for (auto &e : ctx->done) PK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "ticket event");
+    }
+    const int64_t t = ctx->next_ticket;
+    const int k = static_cast<int>(t & 1);
+    const size_t want = staging_bytes(cat->n, elem);
+    if (ctx->aslot_bytes[k] < want) {
+        // a larger slot: nothing may still read or fill the old one
+        PK_CUDA(cudaStreamSynchronize(ctx->copy_stream), "copy stream synchronize");
+        PK_CUDA(cudaEventSynchronize(ctx->slot_free[k]), "slot event synchronize");
+        if ((s = ensure(ctx, &ctx->aslot[k], &ctx->aslot_bytes[k], want, "staging slot")) != PKMOM_OK) return s;
+    }
+    const size_t out_bytes = size_t(PKMOM_NROWS) * p->nbins * sizeof(double);
+    if (ctx->out_bytes < out_bytes) {
+        PK_CUDA(cudaStreamSynchronize(st), "stream synchronize");
+        if ((s = ensure(ctx, reinterpret_cast<void **>(&ctx->out_dev), &ctx->out_bytes, out_bytes, "output")) !=
+            PKMOM_OK)
+            return s;
+    }
+    // fill slot k on the copy stream once the estimate that last read it has moved on
+    PK_CUDA(cudaStreamWaitEvent(ctx->copy_stream, ctx->slot_free[k], 0), "copy stream wait");
+    pkmom_catalog dcat;
+    if ((s = stage_catalog(ctx, *cat, elem, static_cast<char *>(ctx->aslot[k]), ctx->copy_stream, &dcat)) != PKMOM_OK)
+        return s;
+    PK_CUDA(cudaEventRecord(ctx->slot_copied[k], ctx->copy_stream), "slot event");
+    // the estimate on the caller's stream: assign reads the slot, then frees it
+    PK_CUDA(cudaStreamWaitEvent(st, ctx->slot_copied[k], 0), "stream wait");
+    const AssignPlan pl = plan_assign(*p, cat->n, ctx->num_sms, ctx->tune_tile, ctx->tune_list_cap);
+    if ((s = ensure(ctx, &ctx->grids, &ctx->grids_bytes, pkmom_grid_bytes(p->ng, p->precision), "grids")) != PKMOM_OK)
+        return s;
+    if ((s = ensure(ctx, &ctx->scratch, &ctx->scratch_bytes, pl.total, "scratch")) != PKMOM_OK) return s;
+    if (!ctx->moments) PK_CUDA(cudaMalloc(reinterpret_cast<void **>(&ctx->moments), kMomentWords * 8), "moments");
+    if ((s = pkmom_assign(ctx, &dcat, p, ctx->grids, ctx->moments, ctx->scratch, ctx->scratch_bytes, stream)) !=
+        PKMOM_OK)
+        return s;
+    PK_CUDA(cudaEventRecord(ctx->slot_free[k], st), "slot event");
+    if ((s = pkmom_fft(ctx, p, ctx->grids, stream)) != PKMOM_OK) return s;
+    if ((s = pkmom_spectra(ctx, p, ctx->grids, ctx->moments, ctx->out_dev, stream)) != PKMOM_OK) return s;
+    PK_CUDA(cudaMemcpyAsync(out_host, ctx->out_dev, out_bytes, cudaMemcpyDeviceToHost, st), "copy result");
+    PK_CUDA(cudaEventRecord(ctx->done[t % pkmom_ctx::kRing], st), "ticket event");
+    ctx->next_ticket = t + 1;
+    *ticket = t;
+    return PKMOM_OK;
+}
+
+pkmom_status pkmom_wait(pkmom_ctx *ctx, int64_t ticket)
+{
+    if (!ctx) return PKMOM_EINVAL;
+    if (ticket < 0 || ticket >= ctx->next_ticket) return fail(ctx, PKMOM_EINVAL, "unknown ticket");
+    PK_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    // the ring slot holds this ticket or a later one of the same stream: waiting on it
+    // waits at least until this ticket's result is on the host
+    PK_CUDA(cudaEventSynchronize(ctx->done[ticket % pkmom_ctx::kRing]), "ticket synchronize");
+    return check_error_word(ctx);
 }
 
 pkmom_status pkmom_sync(pkmom_ctx *ctx, void *stream)
@@ -604,13 +727,7 @@ pkmom_status pkmom_sync(pkmom_ctx *ctx, void *stream)
     if (!ctx) return PKMOM_EINVAL;
     PK_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
     PK_CUDA(cudaStreamSynchronize(as_stream(stream)), "stream synchronize");
-    int flag = 0;
-    PK_CUDA(cudaMemcpy(&flag, ctx->d_err, sizeof flag, cudaMemcpyDeviceToHost), "read error word");
-    if (flag) {
-        PK_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)), "clear error word");
-        return fail(ctx, PKMOM_EDATA, "catalogue held non-finite or out-of-range positions (|x ng/L| >= 2^30)");
-    }
-    return PKMOM_OK;
+    return check_error_word(ctx);
 }
 
 pkmom_status pkmom_timing_enable(pkmom_ctx *ctx, int on)
@@ -643,6 +760,16 @@ pkmom_status pkmom_timing_read(pkmom_ctx *ctx, double ms[PKMOM_NSTAGES], int64_t
 }
 
 int64_t pkmom_kernel_launches(const pkmom_ctx *ctx) { return ctx ? ctx->st.launches : 0; }
+
+size_t pkmom_context_bytes(const pkmom_ctx *ctx)
+{
+    if (!ctx) return 0;
+    size_t b = sizeof(int) + ctx->grids_bytes + ctx->scratch_bytes + ctx->out_bytes + ctx->staging_bytes +
+               ctx->aslot_bytes[0] + ctx->aslot_bytes[1] + ctx->mu_partials_bytes + ctx->mu_sums_bytes + (ctx->moments ? kMomentWords * 8 : 0);
+    for (const auto &p : ctx->plans) b += p.work;
+    for (const auto &t : ctx->tables) b += t.bytes;
+    return b;
+}
 
 pkmom_status pkmom_set_tuning(pkmom_ctx *ctx, int deposit_tile, int list_cap)
 {

@@ -80,6 +80,7 @@ struct SpectraTables {
     int bin_blocks = 0;
     double *item_partials = nullptr;  // [ng * nbins][kBinVals] (shell-major binning)
     int shell_blocks = 0;
+    size_t bytes = 0;            // device bytes of all the arrays above
 };
 cudaError_t build_spectra_tables(SpectraTables &t, int ng, int order, bool direct, int nbins, double umin,
                                  double umax, int prec, int num_sms, cudaStream_t s, LaunchStats &st);

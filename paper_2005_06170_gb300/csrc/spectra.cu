@@ -21,6 +21,7 @@
 // k_mode_sums in FP64. k_finalize subtracts the shot noise at the shell level in
 // FP64, where the cancellation against large shot noise is harmless.
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "pkmom_internal.cuh"
@@ -598,6 +599,12 @@ cudaError_t build_spectra_tables(SpectraTables &t, int ng, int order, bool direc
                         static_cast<size_t>(ng) * nbins * kBinVals * sizeof(double))) != cudaSuccess)
         return e;
     t.shell_blocks = num_sms * 8;
+    t.bytes = bintab.size() * sizeof(uint16_t) + thresh.size() * sizeof(int) +
+              static_cast<size_t>(ng + nh) * (prec == PKMOM_F32 ? sizeof(float) : sizeof(double)) +
+              static_cast<size_t>(ng + nh) * sizeof(double) +
+              static_cast<size_t>(t.bin_blocks) * kModeVals * nbins * sizeof(double) +
+              static_cast<size_t>(kModeVals + kBinVals) * nbins * sizeof(double) +
+              static_cast<size_t>(ng) * nbins * kBinVals * sizeof(double);
     const size_t smem = static_cast<size_t>(kModeVals) * nbins * sizeof(double);
     if ((e = cudaFuncSetAttribute(k_mode_sums, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem))) !=
         cudaSuccess)
@@ -686,10 +693,9 @@ cudaError_t launch_finalize(const SpectraTables &t, const pkmom_params &p, const
 // ---------------------------------------------------------------------------
 // pkmom_spectra_static: step 4 without any device allocation.
 //
-// Some callers cannot allocate device memory while they run: code inside a CUDA
-// graph that is replayed without host involvement, a host process that owns a
-// fixed memory pool and forbids allocator calls, or a plug-in that must not grow
-// the device footprint after start-up. For them this entry point keeps all of its
+// Some callers cannot allocate device memory while they run: a host process that
+// owns a fixed memory pool and forbids allocator calls, or a plug-in that must not
+// grow the device footprint of the program it runs in after start-up. For them this entry point keeps all of its
 // scratch (shell table, window tables, per-block partial sums, shell sums) in one
 // file-scope device array of kStaticScratchBytes. Every GPU that loads the library
 // holds that array until the process exits. The caller passes the transformed grids,
@@ -792,9 +798,11 @@ StaticLayout static_layout(int ng, int nbins, int nsq_max, size_t elem)
     return L;
 }
 
-// Device address of g_static_scratch, looked up once per device.
+// Device address of g_static_scratch, looked up once per device (under a lock, so that
+// host threads making their first calls at the same time do not race on the cache).
 constexpr int kMaxDevices = 64;
 unsigned char *g_static_ptr[kMaxDevices] = {};
+std::mutex g_static_ptr_lock;
 
 cudaError_t static_scratch_ptr(unsigned char **out)
 {
@@ -802,6 +810,7 @@ cudaError_t static_scratch_ptr(unsigned char **out)
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> guard(g_static_ptr_lock);
     if (!g_static_ptr[dev]) {
         void *ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_static_scratch);
@@ -820,7 +829,8 @@ extern "C" pkmom_status pkmom_spectra_static(const pkmom_params *p, const void *
 {
     using namespace pkmom;
     if (!p || !grids || !moments_dev || !out_dev) return PKMOM_EINVAL;
-    if (!(p->box_L > 0) || p->ng < 16 || p->ng > 1024 || p->ng % 8 || p->order < 1 || p->order > 5 ||
+    if (!(p->box_L > 0) || !std::isfinite(p->box_L) || !std::isfinite(p->theta_scale) || p->ng < 16 ||
+        p->ng > 1024 || p->ng % 8 || p->order < 1 || p->order > 5 ||
         (p->precision != PKMOM_F32 && p->precision != PKMOM_F64) || p->nbins < 1 || p->theta_sn_mode < 0 ||
         p->theta_sn_mode > 1 || (p->bl_radius != 0 && (p->bl_radius < 2 || p->bl_radius > 4 || p->order != 4)))
         return PKMOM_EINVAL;

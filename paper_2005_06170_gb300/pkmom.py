@@ -87,6 +87,10 @@ def lib():
         "pkmom_spectra_mu": (i32, [vp, ctypes.POINTER(Params), vp, vp, ctypes.POINTER(ctypes.c_double), i32, vp, vp]),
         "pkmom_set_tuning": (i32, [vp, i32, i32]),
         "pkmom_assign_scratch_bytes_tuned": (ctypes.c_size_t, [vp, ctypes.POINTER(Params), i64]),
+        "pkmom_context_bytes": (ctypes.c_size_t, [vp]),
+        "pkmom_estimate_host_async": (i32, [vp, ctypes.POINTER(Catalog), ctypes.POINTER(Params), vp, vp,
+                                            ctypes.POINTER(ctypes.c_int64)]),
+        "pkmom_wait": (i32, [vp, i64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -100,7 +104,8 @@ EXPORTED = ("pkmom_params_default", "pkmom_create", "pkmom_destroy", "pkmom_stre
             "pkmom_grid_bytes", "pkmom_assign_scratch_bytes", "pkmom_footprint_bytes", "pkmom_assign",
             "pkmom_fft", "pkmom_spectra", "pkmom_estimate", "pkmom_estimate_host", "pkmom_sync",
             "pkmom_timing_enable", "pkmom_timing_read", "pkmom_kernel_launches", "pkmom_spectra_static",
-            "pkmom_set_tuning", "pkmom_assign_scratch_bytes_tuned", "pkmom_spectra_mu")
+            "pkmom_set_tuning", "pkmom_assign_scratch_bytes_tuned", "pkmom_spectra_mu", "pkmom_context_bytes",
+            "pkmom_estimate_host_async", "pkmom_wait")
 
 
 def params(box_L: float, ng: int, nbins: int, *, order: int = 4, precision: int = F32, kmin_kf: float = 1.0,
@@ -272,6 +277,24 @@ class Context:
                                               _stream_ptr(stream)))
         return out
 
+    def estimate_host_async(self, pos: np.ndarray, vel: np.ndarray, p: Params, out: np.ndarray, mass=None,
+                            stream=None) -> int:
+        """pkmom_estimate_host_async: queues the estimate of a host catalogue (pinned (n,3)
+        arrays) whose (NROWS, nbins) result lands in `out` (a C-contiguous float64 host
+        array); returns the ticket for wait(). The arrays must stay alive and unchanged
+        until then."""
+        cat = catalog_from_numpy(pos, vel, mass)
+        if out.dtype != np.float64 or not out.flags["C_CONTIGUOUS"] or out.size < NROWS * p.nbins:
+            raise ValueError("out must be a C-contiguous float64 array of NROWS * nbins values")
+        t = ctypes.c_int64()
+        self._check(lib().pkmom_estimate_host_async(self._h, ctypes.byref(cat), ctypes.byref(p), out.ctypes.data,
+                                                    _stream_ptr(stream), ctypes.byref(t)))
+        return int(t.value)
+
+    def wait(self, ticket: int):
+        """pkmom_wait: blocks until the result of that ticket is on the host."""
+        self._check(lib().pkmom_wait(self._h, int(ticket)))
+
     def sync(self, stream=None):
         self._check(lib().pkmom_sync(self._h, _stream_ptr(stream)))
 
@@ -294,6 +317,10 @@ class Context:
 
     def scratch_bytes_tuned(self, p: Params, n: int) -> int:
         return int(lib().pkmom_assign_scratch_bytes_tuned(self._h, ctypes.byref(p), n))
+
+    def context_bytes(self) -> int:
+        """Device bytes the context holds (cuFFT plan workspaces, tables, owned buffers)."""
+        return int(lib().pkmom_context_bytes(self._h))
 
 
 def spectra_static(p: Params, grids, moments, out, stream=None):

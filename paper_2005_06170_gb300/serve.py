@@ -35,6 +35,7 @@ class Request:
     future: cf.Future = field(default_factory=cf.Future)
     # filled by the server
     footprint: int = 0
+    ready: object = None     # CUDA event recorded at submit on the producer's stream
     admitted: float = 0.0
     done: float = 0.0
     lane: int = -1
@@ -136,6 +137,9 @@ class Server:
         self.streams = [torch.cuda.Stream(device=device, priority=(hi if k < self.n_small else lo) if split else 0)
                         for k in range(lanes)]
         self.lane_free = [True] * lanes
+        # device memory each lane's context keeps between requests (cuFFT plans and
+        # per-grid tables), charged to the budget beside the running requests
+        self.lane_bytes = [0] * lanes
         self.policy = AdmissionPolicy(int(budget_bytes), max_overtake)
         self.tuner = tuner
         self.gpu = torch.cuda.get_device_name(device)
@@ -150,19 +154,51 @@ class Server:
         self._thread.start()
 
     def footprint(self, req: Request) -> int:
+        """Device bytes a request holds while it runs: the library's own estimate for it
+        (grids, assignment scratch, a cuFFT workspace of a quarter of the grids in case
+        the lane has no plan for this grid yet, staging of a host catalogue), plus the
+        moments and the output. A tuned deposit whose scratch is larger is charged the
+        difference when it starts. A lane's plans and tables that outlive the request
+        are charged separately (lane_bytes)."""
         pk = self._pk
         p = req.params
-        return int(pk.Context.grid_bytes(p.ng, p.precision) + pk.Context.scratch_bytes(p, req.pos.shape[0])
-                   + 16 * 8 + pk.NROWS * p.nbins * 8)
+        return int(pk.Context.footprint_bytes(p, req.pos.shape[0]) + 16 * 8 + pk.NROWS * p.nbins * 8)
+
+    def reserved(self) -> int:
+        """Bytes charged to the budget now: running requests and the lanes' contexts."""
+        return self.in_use + sum(self.lane_bytes)
+
+    def warm(self, grids, nbins: int = 128, box_L: float = 1000.0):
+        """Builds every lane's cuFFT plans and tables for these grid sizes with a tiny
+        estimate (before the first request, so that none pays for it), then charges the
+        memory the lanes' contexts hold."""
+        torch, pk = self._torch, self._pk
+        dev = torch.device("cuda", self.device)
+        g = torch.Generator(device=dev)
+        g.manual_seed(0)
+        pos = torch.rand((4096, 3), generator=g, device=dev) * box_L
+        vel = torch.zeros_like(pos)
+        for ctx, s in zip(self.ctxs, self.streams):
+            s.wait_stream(torch.cuda.current_stream(dev))
+            for ng in grids:
+                ctx.estimate(pos, vel, pk.params(box_L, int(ng), nbins), stream=s)
+        torch.cuda.synchronize(dev)
+        with self._lock:
+            self.lane_bytes = [c.context_bytes() for c in self.ctxs]
 
     def submit(self, req: Request) -> cf.Future:
         req.footprint = self.footprint(req)
         if not req.arrival:
             req.arrival = time.perf_counter()
+        # the catalogue may still be being written on the caller's stream: the lane's
+        # stream waits for this point before it reads it
+        torch = self._torch
+        req.ready = torch.cuda.Event()
+        req.ready.record(torch.cuda.current_stream(req.pos.device))
         with self._lock:
             req.rid = self._next
             self._next += 1
-            if req.footprint > self.policy.budget:
+            if req.footprint + sum(self.lane_bytes) > self.policy.budget:
                 req.future.set_exception(MemoryError(f"request needs {req.footprint} B > budget"))
                 return req.future
             self.queue.append(req)
@@ -187,10 +223,19 @@ class Server:
         if self.tuner is not None:
             tile, cap = self.tuner.choose(ctx, cat, p, self.gpu)
         ctx.set_tuning(tile, cap)
+        n_scratch = ctx.scratch_bytes_tuned(p, cat.n)
+        extra = max(0, n_scratch - pk.Context.scratch_bytes(p, cat.n))
+        if extra:  # a tuned deposit with a larger scratch than the admitted one
+            req.footprint += extra
+            self.in_use += extra
+        if req.ready is not None:
+            s.wait_event(req.ready)
+        for t in (req.pos, req.vel) + ((req.mass,) if req.mass is not None else ()):
+            t.record_stream(s)  # the allocator keeps the catalogue until the lane is done
         with torch.cuda.stream(s):
             grids = torch.empty(pk.Context.grid_bytes(p.ng, p.precision) // item, dtype=dt, device=dev)
             mom = torch.zeros(16, dtype=torch.float64, device=dev)
-            scratch = torch.empty(ctx.scratch_bytes_tuned(p, cat.n), dtype=torch.uint8, device=dev)
+            scratch = torch.empty(n_scratch, dtype=torch.uint8, device=dev)
             out = torch.empty((pk.NROWS, p.nbins), dtype=torch.float64, device=dev)
             host = torch.empty((pk.NROWS, p.nbins), dtype=torch.float64, pin_memory=True)
         ctx.assign(cat, p, grids, mom, scratch, stream=s)
@@ -230,11 +275,20 @@ class Server:
                 if not free:
                     start = []
                 elif self.strict:
-                    start = self.policy.admit(self.queue, len(free), self.in_use,
+                    start = self.policy.admit(self.queue, len(free), self.reserved(),
                                               free_large=sum(k >= self.n_small for k in free),
                                               is_large=lambda r: r.footprint > self.large_bytes)
                 else:
-                    start = self.policy.admit(self.queue, len(free), self.in_use)
+                    start = self.policy.admit(self.queue, len(free), self.reserved())
+                if not start and not self.inflight and self.queue:
+                    # nothing runs and the oldest request still does not fit beside the
+                    # lanes' own memory: it never will
+                    head = self.queue[0]
+                    if head.footprint + self.reserved() > self.policy.budget:
+                        self.queue.pop(0)
+                        head.future.set_exception(MemoryError(
+                            f"request needs {head.footprint} B beside {self.reserved()} B held by the lanes "
+                            f"> budget {self.policy.budget} B"))
                 for r in start:
                     self.queue.remove(r)
                     self.in_use += r.footprint
@@ -260,7 +314,11 @@ class Server:
                             err = e
                         self.lane_free[lane] = True
                         self.in_use -= req.footprint
+                        self.lane_bytes[lane] = self.ctxs[lane].context_bytes()
                         self.completed.append(req)
+                        # the server no longer needs the catalogue (the lane's stream,
+                        # recorded on it, has finished): release it for the caller
+                        req.pos = req.vel = req.mass = None
                         if err is None:
                             req.future.set_result(host.numpy().copy())
                         else:

@@ -152,7 +152,10 @@ def test_serving_admits_by_footprint(gpu_lib):
     probe = Server(lanes=1)
     fp = max(probe.footprint(Request(d["pos"], d["vel"], p)) for d, p in zip(devs, params))
     probe.close()
-    srv = Server(lanes=4, budget_bytes=int(1.5 * fp))  # room for one request at a time
+    srv = Server(lanes=4, budget_bytes=1e12)
+    srv.warm((64,), nbins=8)  # every lane's plan and tables, charged to the budget
+    assert all(b > 0 for b in srv.lane_bytes) and srv.reserved() == sum(srv.lane_bytes)
+    srv.policy.budget = srv.reserved() + int(1.5 * fp)  # room for one request at a time
     futs = [srv.submit(Request(d["pos"], d["vel"], p)) for d, p in zip(devs, params)]
     for f in futs:
         f.result(timeout=120)
@@ -163,3 +166,31 @@ def test_serving_admits_by_footprint(gpu_lib):
     with pytest.raises(MemoryError):
         srv.submit(big).result(timeout=10)
     srv.close()
+
+
+def test_served_catalogue_written_on_the_callers_stream(gpu_lib):
+    """A request whose catalogue is still being written on the caller's stream when it is
+    submitted: the lane waits for that point of the caller's stream before reading it."""
+    import torch
+
+    from paper_2005_06170_gb300.serve import Request, Server
+    pk = gpu_lib
+    c, L, ng = _mixed(seed=9)[2]
+    d = _dev(c, torch)
+    p = pk.params(L, ng, 10)
+    ctx = pk.Context(0)
+    ref = _single(pk, ctx, d, p)
+    ctx.close()
+    srv = Server(lanes=2)
+    side = torch.cuda.Stream()
+    pos = torch.zeros_like(d["pos"])
+    vel = torch.zeros_like(d["vel"])
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        torch.cuda._sleep(20_000_000)  # the copy below lands well after the submit
+        pos.copy_(d["pos"])
+        vel.copy_(d["vel"])
+        fut = srv.submit(Request(pos, vel, p))
+    got = fut.result(timeout=120)
+    srv.close()
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.nanmax(np.abs(ref)), equal_nan=True)

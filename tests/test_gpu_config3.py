@@ -1,7 +1,9 @@
 """Full-size Zel'dovich workload: 512^3 particles in L = 1500 Mpc/h, grids 512^3 and 1024^3.
 
-512^3 grid: the GPU against the FP64 oracle on every shell (1e-4).
-1024^3 grid (too large for the oracle here): properties that hold at any size --
+512^3 and 1024^3 grids: the GPU against the FP64 oracle on every shell (1e-4), both
+bulk-flow variants. The oracle's 1024^3 run holds about 80 GB of host memory (four FP64
+grids and their four complex128 half spectra) and takes a few minutes.
+1024^3 grid, in addition: properties that hold at any size --
 exact shell mode counts (a brute-force count of integer vectors), shot-noise rows
 against the oracle's moments (per shell SN_pp / SN_dd = tr Q / sum m^2, Eqs. rawPp
 and psn), the bulk-flow identity Re P_dtheta' = Re P_dtheta (Eq. bfpdpx), and the
@@ -50,6 +52,17 @@ def test_config3_ng512_matches_oracle(cat, dev, gpu_lib):
     print(f"512^3 particles on a 512^3 grid: worst normalised shell error {worst:.3e}")
 
 
+def test_config3_ng1024_matches_oracle(cat, dev, gpu_lib):
+    import time
+    from test_gpu_parity import compare
+    g = _run(gpu_lib, dev, 1024)
+    t0 = time.perf_counter()
+    o = est.estimate(cat["pos"], cat["vel"], L=L, ng=1024, nbins=NB)
+    worst = compare(g, o, 1e-4)
+    print(f"512^3 particles on a 1024^3 grid: worst normalised shell error {worst:.3e} "
+          f"(oracle {time.perf_counter() - t0:.0f} s)")
+
+
 def _shell_counts(ng, nbins, umax):
     """Full-sphere mode counts per shell (linear bins in |n| on [1, umax]) by counting
     the integer vectors n with |n|^2 = m, components in [-ng/2, ng/2)."""
@@ -94,11 +107,15 @@ def test_config3_ng1024_properties(cat, dev, gpu_lib):
         np.testing.assert_allclose(out["P_dt_b"], out["P_dt"], rtol=1e-5,
                                    atol=1e-5 * np.max(np.abs(out["P_dt"])))
 
-    # Sec. 2.4.3: two resolutions agree below half the coarser Nyquist frequency
-    half = NB // 2
-    worst = {}
+    # Sec. 2.4.3: two resolutions agree below half the coarser Nyquist frequency (the
+    # paper: under 0.2 % there); the report gives the scale where each spectrum's
+    # difference first exceeds 1 % (paper, BL3: 0.87, 0.82, 0.74, 0.85 k_N for P_p,
+    # P_theta, P_delta-theta, P_delta) and the largest difference below 0.7 k_N
+    from paper_2005_06170_gb300.aliasing import compare_pair
+    rep = compare_pair(raw512, raw1024, np.pi * 512 / L)
     for key in ("P_dd", "P_pp", "P_tt", "P_dt", "P_pp_b", "P_tt_b"):
-        rel = np.abs(raw1024[key][:half] / raw512[key][:half] - 1)
-        worst[key] = float(rel.max())
-        assert np.all(rel < 2e-3), (key, rel.max(), rel.argmax())
-    print("1024^3 vs 512^3 grid, raw spectra below k_N(512)/2: max relative difference", worst)
+        assert rep[key]["max_dev_k_le_0.5kN"] < 2e-3, (key, rep[key])
+    print("1024^3 vs 512^3 grid, raw spectra (k / k_N of the 512^3 grid):")
+    for key, r in rep.items():
+        print(f"  {key}: first above 1 % at {r['first_k_over_kN_above']}, max below 0.5 k_N "
+              f"{r['max_dev_k_le_0.5kN']:.2e}, below 0.7 k_N {r['max_dev_k_le_0.7kN']:.2e}")

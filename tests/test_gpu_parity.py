@@ -1,6 +1,6 @@
 """GPU library vs the FP64 CPU oracle, through the C-ABI, on the same seeded inputs.
 
-Tolerances ("Parity"): FP64 mode 1e-9 and FP32 grids 1e-4, relative
+Tolerances: FP64 mode 1e-9 and FP32 grids 1e-4, relative
 per k-shell, with a floor at the shell's shot-noise fluctuation scale SN_b/sqrt(n_b)
 for shells whose noise-subtracted value is near zero.
 """
@@ -19,11 +19,8 @@ KEYS = ("P_dd", "P_pp", "P_tt", "P_dt")
 KEYS_B = ("P_pp_b", "P_tt_b", "P_dt_b")
 
 
-def compare(gpu: dict, ora: dict, rtol: float, bulk: bool = True, raw_floor: bool = False):
-    """Per-shell relative error with the shot-noise floor; returns the worst value.
-
-    raw_floor: measure the error against the shell's raw power |P| + SN instead (for
-    degenerate catalogues whose node sums cancel, where FP32 grids cannot do better)."""
+def compare(gpu: dict, ora: dict, rtol: float, bulk: bool = True):
+    """Per-shell relative error with the shot-noise floor; returns the worst value."""
     n = ora["n_modes"]
     np.testing.assert_array_equal(gpu["n_modes"], n)
     ok = n > 0
@@ -45,8 +42,6 @@ def compare(gpu: dict, ora: dict, rtol: float, bulk: bool = True, raw_floor: boo
             unsub = np.abs(ora[base][ok]) + (ora[SN_OF[base]][ok] if base in SN_OF else
                                              np.sqrt(ora["SN_dd"][ok] * ora["SN_tt"][ok]))
             floor = np.maximum(floor, 100.0 * eps / rtol * unsub)
-        if raw_floor:
-            floor = np.maximum(floor, np.sqrt(n[ok]) * floor)
         scale = np.maximum(np.abs(o), floor)
         err = np.abs(g - o) / scale
         worst = max(worst, float(err.max()))
@@ -293,8 +288,10 @@ def test_single_particle_and_wrapped_positions(ctx, gpu_lib):
 
 
 def test_all_particles_in_one_cell(ctx, gpu_lib):
-    """Dense catalogue: every particle in the same cell (shared-memory contention,
-    2e4 contributions per node whose momentum sums cancel): 1e-4 of the raw power."""
+    """Dense catalogue: every particle in two neighbouring cells (shared-memory
+    contention, 2e4 contributions per node whose momentum sums cancel), held to the
+    normal shot-noise floor. An FP64 emulation of FP32 grids and an FP32 FFT of the same
+    catalogue stays within 2e-6 of that floor, so FP32 arithmetic needs no wider one."""
     pk = gpu_lib
     rng = np.random.default_rng(51)
     L, ng, n = 100.0, 32, 20000
@@ -302,7 +299,8 @@ def test_all_particles_in_one_cell(ctx, gpu_lib):
     vel = rng.normal(0, 100, size=(n, 3)).astype(np.float32)
     cat = {"pos": pos, "vel": vel, "L": L}
     p = pk.params(L, ng, 8)
-    compare(run_gpu(ctx, pk, cat, p), run_oracle(cat, L, ng, 8), 1e-4, raw_floor=True)
+    worst = compare(run_gpu(ctx, pk, cat, p), run_oracle(cat, L, ng, 8), 1e-4)
+    print(f"all particles in one cell: worst normalised shell error {worst:.3e}")
 
 
 def test_positions_on_the_box_edge_fp32(ctx, gpu_lib):

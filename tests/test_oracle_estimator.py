@@ -322,3 +322,31 @@ def test_zeldovich_linear_theory_ratios():
     assert np.all(out["P_dt"][:8] > 0)
     assert np.all(np.abs(r1 - 1) < 0.02), r1
     assert np.all(np.abs(r2 - 1) < 0.03), r2
+
+
+def test_fp32_grids_meet_the_shot_noise_floor_on_a_one_cell_catalogue():
+    """The parity tolerance for FP32 grids (1e-4 of max(|P_b|, SN_b / sqrt(n_b))) is met
+    by FP32 arithmetic itself on the most degenerate catalogue the GPU tests use: 2e4
+    particles in two neighbouring cells, whose momentum node sums cancel. The oracle's
+    grids rounded to FP32 and transformed by an FP32 FFT stay within 1e-5 of that
+    floor (measured 1.6e-6), so the GPU test holds that case to the normal floor."""
+    import scipy.fft
+    rng = np.random.default_rng(51)
+    L, ng, n = 100.0, 32, 20000
+    pos = (10.0 + rng.uniform(0, L / ng, size=(n, 3))).astype(np.float32)
+    vel = rng.normal(0, 100, size=(n, 3)).astype(np.float32)
+    ref = est.estimate(pos, vel, L=L, ng=ng, nbins=8)
+    mom = est.moments(vel)
+    grids = est.assign(pos, vel, None, L=L, ng=ng)
+    F32 = np.stack([scipy.fft.rfftn(g.astype(np.float32)) for g in grids])
+    assert F32.dtype == np.complex64
+    emu = est.spectra_from_fourier(F32.astype(np.complex128), mom, L=L, ng=ng, nbins=8)
+    nm = ref["n_modes"]
+    for key in ("P_dd", "P_pp", "P_tt", "P_dt", "P_pp_b", "P_tt_b", "P_dt_b"):
+        sfx = "_b" if key.endswith("_b") else ""
+        if key.startswith("P_dt"):
+            floor = np.sqrt(ref["SN_dd"] * ref["SN_tt" + sfx]) / np.sqrt(nm)
+        else:
+            floor = ref["SN_" + key[2:]] / np.sqrt(nm)
+        err = np.abs(emu[key] - ref[key]) / np.maximum(np.abs(ref[key]), floor)
+        assert np.max(err) < 1e-5, (key, np.max(err))
