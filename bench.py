@@ -57,12 +57,24 @@ DEFAULT = "zeldovich512_ng512"
 # DRAM bytes (read + write) per launch of the dominant stage's kernels, from one ncu
 # capture of the current kernels; a stage whose kernels change drops its entry until
 # it is captured again
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    ("zeldovich512_ng512", "deposit"): ((4905.6 + 3595.1 + 3714.8 + 1623.7) * 1e6,
+                                        "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_deposit_home and "
+                                        "k_home_fixup, mean of 5 launches of the 512^3 workload "
+                                        "(profiles/launches_zeldovich512_ng512.md)"),
+}
+# warp instructions per launch of the dominant kernel, from one ncu --set full capture of
+# the current kernel on the 256^3 workload, scaled to other workloads by particle count
+# (the same work per particle at one particle per cell)
+MEASURED_INSTRUCTIONS = {
+    "k_deposit_home": (661.98e6, 256 ** 3, "ncu smsp__inst_executed.sum of k_deposit_home on the 256^3 workload "
+                                         "(profiles/kernels_zeldovich256_ng256.md), scaled by particles"),
+}
 # configs 4 and 5 run through their own drivers below
 MULTI = {
     "batch64": "64 catalogues in one launch sequence: particle counts log-uniform in [1e5, 2e7], seeded "
                "Zel'dovich or Poisson (50/50), grids from {128, 256, 384}^3, L in [300, 1500] Mpc/h, "
-               "FP32, 128 shells; lanes + CUDA graph + autotuned tiles",
+               "FP32, 128 shells; persistent deposit and binning kernels + CUDA graph + autotuned tiles",
     "serve": "Poisson arrivals of estimation requests, each its own seeded Poisson catalogue drawn on the "
              "device at arrival, particle counts log-uniform in [1e5, 1.3e8], grids from {128, 256, 512, "
              "1024}^3, FP32, 128 shells, admitted by HBM footprint against 180 GB",
@@ -284,7 +296,17 @@ def roofline(workload, stage_ms, n, ng, prec, bl_radius, unit_mass=True):
     gbs = alg_bytes / (ms * 1e-3) / 1e9 if ms > 0 else None
     tflops = flops / (ms * 1e-3) / 1e12 if ms > 0 else None
     traffic = None if bl_radius else MEASURED_TRAFFIC.get((workload, "deposit"))
-    return {"kernel": deposit_kernels(n, ng, prec, bl_radius), "bound": "alu", "achieved": tflops,
+    kern = deposit_kernels(n, ng, prec, bl_radius)
+    issue = None
+    ins = MEASURED_INSTRUCTIONS.get(kern.split(" ")[0])
+    if ins and ms > 0:
+        per_launch = ins[0] * n / ins[1]
+        rate = per_launch / (ms * 1e-3)
+        issue = {"warp_instructions_per_launch": per_launch, "achieved": rate, "peak": ISSUE_PEAK_WARP_INSTR,
+                 "unit": "warp instructions/s", "frac": rate / ISSUE_PEAK_WARP_INSTR,
+                 "peak_source": "derived: 152 SMs x 4 schedulers x 2070 MHz", "source": ins[2],
+                 "note": "time of the whole stage (with k_home_fixup), so the kernel's own rate is higher"}
+    return {"kernel": kern, "bound": "alu", "achieved": tflops,
             "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": (tflops / FP32_PEAK_TFLOPS) if tflops else None,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz",
             "algorithmic_flops_per_launch": flops,
@@ -292,7 +314,7 @@ def roofline(workload, stage_ms, n, ng, prec, bl_radius, unit_mass=True):
             "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": (gbs / peak) if gbs else None,
                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                     else "fallback", "algorithmic_bytes_per_launch": alg_bytes},
-            "avg_launch_ms": ms}
+            "issue": issue, "avg_launch_ms": ms}
 
 
 def bin_roofline(stage_ms, ng, prec):
@@ -369,24 +391,33 @@ def batch64(args, torch):
     torch.cuda.synchronize()
     n_total = sum(int(c["pos"].shape[0]) for c in cats)
     cells = sum(int(p.ng) ** 3 for p in params)
-    runner = BatchRunner(cats, params, lanes=8, use_graph=True, tuner=Autotuner(repeats=2))
-    runner.run()  # tuning, eager pass, capture
     origin = torch.cuda.current_stream(dev)
     steps = max(3, args.batch_steps)
-    for _ in range(3):
-        runner.run()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(_clock_id(torch, dev))
-    l0 = runner.kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(origin)
-    for _ in range(steps):
-        runner.run()
-    e1.record(origin)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    clk = clocks.stop()
-    runner.close()
+    timed = {}
+    clk = None
+    launches = 0
+    for mode in ("fused", "lanes"):
+        runner = BatchRunner(cats, params, lanes=8, use_graph=True, tuner=Autotuner(repeats=2),
+                             fused=mode == "fused")
+        l0 = runner.kernel_launches()
+        runner.run()  # tuning, eager pass, capture
+        if mode == "fused":
+            launches = runner.kernel_launches() - l0
+        for _ in range(3):
+            runner.run()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(_clock_id(torch, dev)) if mode == "fused" else None
+        e0.record(origin)
+        for _ in range(steps):
+            runner.run()
+        e1.record(origin)
+        torch.cuda.synchronize()
+        timed[mode] = e0.elapsed_time(e1) / steps
+        if clocks is not None:
+            clk = clocks.stop()
+        runner.close()
+    ms = timed["fused"]
     ctx = pkmom.Context(0)
     outs = [torch.empty((pkmom.NROWS, p.nbins), dtype=torch.float64, device=dev) for p in params]
     for c, p, o in zip(cats, params, outs):
@@ -402,6 +433,9 @@ def batch64(args, torch):
     ctx.close()
     return {"workload": MULTI["batch64"], "n_particles": n_total, "cells": cells, "steps": steps,
             "batched_ms": ms, "plain_ms": ms_plain, "batched_over_plain": ms_plain / ms,
+            "batched": "pkmom_estimate_batch (persistent deposit and binning kernels) in one CUDA graph",
+            "lanes_ms": timed["lanes"], "lanes": "8 lanes (contexts and streams) in one CUDA graph",
+            "kernel_launches_per_batch": int(launches),
             "batched_particles_per_s": n_total / (ms * 1e-3), "plain_particles_per_s": n_total / (ms_plain * 1e-3),
             "batched_Mcells_per_s": cells / (ms * 1e-3) / 1e6, "clocks": clk,
             "note": "graph replays launch no kernels from the host; the count is of the eager pass"}
@@ -430,9 +464,21 @@ def serve(args, torch, rate, nreq, warm=20):
     L = 1000.0
     params = [pkmom.params(L, int(g), 128) for g in grids]
     result = {}
-    for name, lanes in (("served", 4), ("plain", 1)):
-        srv = Server(lanes=lanes, budget_bytes=180e9)
+    arms = [a for a in (("served", args.serve_lanes), ("plain", 1)) if not args.serve_only or a[0] == args.serve_only]
+    for name, lanes in arms:
+        srv = Server(lanes=lanes, budget_bytes=180e9, large_priority=args.serve_priority)
         srv.warm((128, 256, 512, 1024), nbins=128, box_L=L)
+        # a burst of the extreme sizes before the clock starts: the first launch of every
+        # kernel and the allocator's first blocks of each size are not part of the trace
+        burst = []
+        for g in (128, 256, 512, 1024):
+            for k, n in enumerate((100_000, int(counts.max()))):
+                c = catalogs.poisson_torch(n, L, seed=90_000 + 10 * g + k, device=dev)
+                burst.append(srv.submit(Request(c["pos"], c["vel"], pkmom.params(L, g, 128))))
+                del c
+        for f in burst:
+            f.result(timeout=600)
+        srv.completed.clear()
         clocks = ClockSampler(_clock_id(torch, dev)) if name == "served" else None
         futs = []
         reqs = []
@@ -485,7 +531,9 @@ def run_batch64(args):
             "config": {"workload": MULTI["batch64"], "n_particles": b["n_particles"], "cells": b["cells"],
                        "l2": "inputs larger than L2, no flush"},
             "Mcells_per_s": b["batched_Mcells_per_s"], "plain_value": b["plain_particles_per_s"],
-            "plain_ms_per_step": b["plain_ms"], "batched_over_plain": b["batched_over_plain"], "clocks": b["clocks"]}
+            "plain_ms_per_step": b["plain_ms"], "batched_over_plain": b["batched_over_plain"],
+            "lanes_ms_per_step": b["lanes_ms"], "batched": b["batched"], "lanes": b["lanes"],
+            "gpu_launches": b["kernel_launches_per_batch"], "clocks": b["clocks"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -495,15 +543,16 @@ def run_serve(args):
     reps = []
     for k in range(max(1, args.repeats)):
         reps.append(serve(args, torch, args.rate, args.requests))
-    sv, pl = reps[0]["served"], reps[0]["plain"]
-    line = {"metric": METRIC, "value": sv["throughput_particles_per_s"], "unit": "particles/s", "n_gpus": 1,
-            "steps": args.requests, "warmup": 20, "ms_per_step": sv["mean_ms"], "higher_is_better": True,
+    sv, pl = reps[0].get("served", {}), reps[0].get("plain", {})
+    head = sv or pl
+    line = {"metric": METRIC, "value": head["throughput_particles_per_s"], "unit": "particles/s", "n_gpus": 1,
+            "steps": args.requests, "warmup": 20, "ms_per_step": head["mean_ms"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": MULTI["serve"], "requests": args.requests, "rate_per_s": args.rate},
-            "latency_ms": {"p50": sv["p50_ms"], "p99": sv["p99_ms"]},
-            "plain": pl, "served": sv, "repeats": [{"served": {k: r["served"][k] for k in ("p50_ms", "p99_ms")},
-                                                    "plain": {k: r["plain"][k] for k in ("p50_ms", "p99_ms")}}
-                                                   for r in reps],
+            "config": {"workload": MULTI["serve"], "requests": args.requests, "rate_per_s": args.rate,
+                       "lanes": args.serve_lanes, "large_priority": args.serve_priority},
+            "latency_ms": {"p50": head["p50_ms"], "p99": head["p99_ms"]},
+            "plain": pl, "served": sv, "repeats": [{a: {k: r[a][k] for k in ("p50_ms", "p99_ms")}
+                                                    for a in ("served", "plain") if a in r} for r in reps],
             "clocks": reps[0].get("clocks")}
     print(json.dumps(line), flush=True)
     return 0
@@ -519,6 +568,11 @@ def main(argv=None):
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
     ap.add_argument("--repeats", type=int, default=1, help="serve: repeats of the whole trace")
     ap.add_argument("--batch-steps", type=int, default=5, help="batch64: timed replays")
+    ap.add_argument("--serve-lanes", type=int, default=4, help="serve: lanes of the served run")
+    ap.add_argument("--serve-priority", default="low", choices=["low", "same", "high"],
+                    help="serve: stream priority of the lane for large requests")
+    ap.add_argument("--serve-only", default="", choices=["", "served", "plain"],
+                    help="serve: run only one of the two arms")
     ap.add_argument("--tile", type=int, default=-1, help="deposit tile id (pkmom_set_tuning); -1 = automatic")
     ap.add_argument("--bl-radius", type=int, default=0,
                     help="0: exact BL kernel; 2..4: the BL function truncated to that many cells, deposited directly")

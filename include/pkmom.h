@@ -172,9 +172,10 @@ size_t pkmom_footprint_bytes(const pkmom_params *p, int64_t n);
 
 /* Steps 1-2 (Secs. 2.1-2.2, 2.4.1): moments of the catalogue into *moments_dev
  * (a device pkmom_moments) and the B-spline assignment of (m, m v) onto the four
- * grids at `grids` (pkmom_grid_bytes bytes, device; every real element is
- * written, the two padding elements of each row are not). `scratch` is device
- * memory of at least pkmom_assign_scratch_bytes bytes (else PKMOM_ESCRATCH). */
+ * grids at `grids` (pkmom_grid_bytes bytes, device, 16-byte aligned; every real
+ * element is written, the two padding elements of each row are not). `scratch` is
+ * 16-byte aligned device memory of at least pkmom_assign_scratch_bytes bytes (else
+ * PKMOM_ESCRATCH). Misaligned grids or scratch give PKMOM_EINVAL. */
 pkmom_status pkmom_assign(pkmom_ctx *ctx, const pkmom_catalog *cat, const pkmom_params *p,
                           void *grids, void *moments_dev, void *scratch, size_t scratch_bytes,
                           void *stream);
@@ -257,6 +258,41 @@ pkmom_status pkmom_wait(pkmom_ctx *ctx, int64_t ticket);
 pkmom_status pkmom_spectra_static(const pkmom_params *p, const void *grids, const void *moments_dev,
                                   double *out_dev, void *stream);
 
+/* One catalogue of a batched estimate (pkmom_estimate_batch): the device catalogue, its
+ * parameters, the caller-owned device buffers its steps write (as for pkmom_assign and
+ * pkmom_spectra) and its deposit tuning (pkmom_set_tuning's values; -1: automatic). */
+typedef struct {
+    pkmom_catalog cat;
+    pkmom_params p;
+    void *grids;          /* pkmom_grid_bytes(p.ng, p.precision) bytes, 16-byte aligned */
+    void *moments_dev;    /* 16 doubles */
+    void *scratch;        /* pkmom_assign_scratch_bytes_tuned for this tuning, 16-byte aligned */
+    size_t scratch_bytes;
+    double *out_dev;      /* PKMOM_NROWS * p.nbins doubles */
+    int deposit_tile, list_cap;
+} pkmom_batch_item;
+
+enum { PKMOM_BATCH_MAX = 128 };
+
+/* Device bytes of the work buffer pkmom_estimate_batch needs for these items (0 for bad
+ * arguments): per FP32 catalogue its binning partials (ng * nbins * 7 doubles) and shell
+ * sums, and a work counter. */
+size_t pkmom_batch_work_bytes(int n, const pkmom_batch_item *items);
+
+/* Steps 1-4 of n <= PKMOM_BATCH_MAX catalogues of any sizes in one launch sequence on one
+ * stream (the batched workload of many catalogues): the moments and sort of each
+ * catalogue; ONE persistent deposit kernel over the tiles of every catalogue that takes
+ * the 16^3 gather deposit (cubic order, FP32, exact BL kernel; each CTA takes (catalogue,
+ * tile) items from a work counter until none is left, with no waits between items), the
+ * others deposited one by one; the FFTs; ONE persistent binning kernel over the (slab,
+ * shell) items of every FP32 catalogue, the FP64 ones binned one by one. Each result
+ * equals pkmom_estimate's on that catalogue with the same tuning. work: device memory of
+ * at least pkmom_batch_work_bytes (else PKMOM_ESCRATCH). The first call for a grid size
+ * builds its cuFFT plan and tables (this allocates; call once before any stream
+ * capture); later calls allocate nothing and can be captured. */
+pkmom_status pkmom_estimate_batch(pkmom_ctx *ctx, int n, const pkmom_batch_item *items, void *work,
+                                  size_t work_bytes, void *stream);
+
 /* Wait for the stream and return any latched device-side error (PKMOM_EDATA). */
 pkmom_status pkmom_sync(pkmom_ctx *ctx, void *stream);
 
@@ -273,6 +309,17 @@ pkmom_status pkmom_timing_read(pkmom_ctx *ctx, double ms[PKMOM_NSTAGES], int64_t
 
 /* Number of kernels this context has launched (its own kernels; cuFFT's not counted). */
 int64_t pkmom_kernel_launches(const pkmom_ctx *ctx);
+
+/* 1 for the checked build (libpkmom_checked.so), 0 otherwise. The checked build tests
+ * every grid, halo, shared-buffer, sort-key, record and bin index before its access,
+ * skips the access when the test fails and reports it as PKMOM_EDATA from pkmom_sync
+ * (or the next synchronising call); the same results otherwise, more slowly. */
+int pkmom_checked(void);
+
+/* Checked build only (PKMOM_EUNSUPPORTED otherwise): launches one kernel whose single
+ * index test fails on purpose (no access follows it), so that the next pkmom_sync
+ * returns PKMOM_EDATA: a test of the reporting path. */
+pkmom_status pkmom_checked_selftest(pkmom_ctx *ctx, void *stream);
 
 /* Device bytes this context holds now: the workspaces of its cached cuFFT plans, its
  * cached per-grid tables and the buffers that pkmom_estimate, pkmom_estimate_host(_async)

@@ -56,16 +56,21 @@ class Autotuner:
     def key(gpu: str, ng: int, precision: int, n: int) -> str:
         return f"{gpu}|ng={ng}|prec={precision}|dc={density_class(n, ng)}"
 
-    def choose(self, ctx, cat, p, gpu: str = "gpu") -> tuple[int, int]:
-        """Tuning for this request: cached, or measured now (cat: the pkmom Catalog)."""
+    def choose(self, ctx, cat, p, gpu: str = "gpu", tiles=None) -> tuple[int, int]:
+        """Tuning for this request: cached, or measured now (cat: the pkmom Catalog).
+        tiles: the deposit tiles to choose from (default all that divide the grid)."""
         k = self.key(gpu, p.ng, p.precision, cat.n)
+        cands = candidates(p.ng, p.precision)
+        if tiles is not None:
+            k += "|tiles=" + ",".join(str(t) for t in sorted(tiles))
+            cands = [c for c in cands if c[0] in tiles] or cands
         with self._lock:
             if k in self.table:
                 e = self.table[k]
                 return e["tile"], e["list_cap"]
         best = None
         trials = {}
-        for tile, cap in candidates(p.ng, p.precision):
+        for tile, cap in cands:
             ms = self.timer(ctx, cat, p, tile, cap)
             trials[f"{tile},{cap}"] = ms
             if best is None or ms < best[0]:

@@ -1,19 +1,26 @@
 """Batched estimation of many catalogues of uneven sizes and grids (one GPU).
 
-The catalogues are dealt to a few lanes (largest first, each to the least loaded
-lane); a lane owns a libpkmom context (its own cuFFT plans and tables: a cuFFT plan
-must not run on two streams at once) and a CUDA stream, so the lanes' catalogues
-overlap on the device. Every catalogue has its own grids, scratch, moments and
-output, allocated once. The first run is eager (it builds plans and tables and
-runs the autotuner); it is then captured into one CUDA graph (fork to the lanes'
-streams, join back), which later runs replay with a single launch.
+Two ways to run a batch:
+
+* fused (default): one libpkmom context and one stream; the whole batch is one call of
+  pkmom_estimate_batch, which sorts each catalogue, deposits every catalogue that takes
+  the gather deposit in ONE persistent kernel (CTAs draw (catalogue, tile) items from a
+  work counter) and bins every FP32 catalogue in ONE persistent kernel;
+* lanes: the catalogues are dealt to a few lanes (largest first, each to the least
+  loaded lane); a lane owns a context (its own cuFFT plans and tables: a cuFFT plan must
+  not run on two streams at once) and a CUDA stream, and runs its catalogues one after
+  another, so the lanes' catalogues overlap on the device.
+
+Every catalogue has its own grids, scratch, moments and output, allocated once. The
+first run is eager (it builds plans and tables and runs the autotuner); it is then
+captured into one CUDA graph, which later runs replay with a single launch.
 """
 from __future__ import annotations
 
 import torch
 
 from . import pkmom
-from .autotune import Autotuner
+from .autotune import HOME_TILE, Autotuner
 
 
 def deal(costs: list[float], lanes: int) -> list[int]:
@@ -33,16 +40,18 @@ class _Item:
 
 class BatchRunner:
     def __init__(self, catalogs: list[dict], params: list, lanes: int = 4, use_graph: bool = True,
-                 tuner: Autotuner | None = None, device: int = 0):
+                 tuner: Autotuner | None = None, device: int = 0, fused: bool = True):
         """catalogs: dicts with CUDA tensors pos (n,3), vel (n,3), optional mass (n,);
-        params: one pkmom.Params per catalogue."""
+        params: one pkmom.Params per catalogue. fused: one pkmom_estimate_batch call per
+        run (persistent deposit and binning kernels); otherwise `lanes` lanes."""
         if len(catalogs) != len(params):
             raise ValueError("one Params per catalogue")
         self.device = device
         self.use_graph = use_graph
         self.tuner = tuner
+        self.fused = fused
         self.gpu = torch.cuda.get_device_name(device)
-        nl = max(1, min(lanes, len(catalogs)))
+        nl = 1 if fused else max(1, min(lanes, len(catalogs)))
         self.ctxs = [pkmom.Context(device) for _ in range(nl)]
         self.streams = [torch.cuda.Stream(device=device) for _ in range(nl)]
         self.items: list[_Item] = []
@@ -63,7 +72,9 @@ class BatchRunner:
         for it in self.items:
             ctx = self.ctxs[it.lane]
             if self.tuner is not None:
-                it.tile, it.cap = self.tuner.choose(ctx, it.cat, it.p, self.gpu)
+                # fused: the tiles the persistent deposit takes (16^3 gather) or the home tiles
+                it.tile, it.cap = self.tuner.choose(ctx, it.cat, it.p, self.gpu,
+                                                    tiles=(0, HOME_TILE) if self.fused else None)
             else:
                 it.tile, it.cap = -1, -1
             ctx.set_tuning(it.tile, it.cap)
@@ -76,10 +87,23 @@ class BatchRunner:
             it.mom = torch.zeros(16, dtype=torch.float64, device=dev)
             it.scratch = torch.empty(n_scratch, dtype=torch.uint8, device=dev)
             it.out = torch.empty((pkmom.NROWS, it.p.nbins), dtype=torch.float64, device=dev)
+        if self.fused:
+            self._chunks = []
+            for k in range(0, len(self.items), pkmom.BATCH_MAX):
+                part = self.items[k:k + pkmom.BATCH_MAX]
+                arr = pkmom.batch_items([(it.cat, it.p, it.grids, it.mom, it.scratch, it.out, it.tile, it.cap)
+                                         for it in part])
+                work = torch.empty(pkmom.batch_work_bytes(arr), dtype=torch.uint8,
+                                   device=torch.device("cuda", self.device))
+                self._chunks.append((arr, work))
         self._prepared = True
 
     def _issue(self, lane: int):
         ctx, s = self.ctxs[lane], self.streams[lane]
+        if self.fused:
+            for arr, work in self._chunks:
+                ctx.estimate_batch(arr, work, stream=s)
+            return
         for it in self.items:
             if it.lane != lane:
                 continue

@@ -16,6 +16,7 @@
 //   k_deposit(_fx)  one CTA per output tile gathers the particles of every segment whose
 //                   stencils reach the tile, accumulates in shared memory, then writes
 //                   each node of the tile exactly once. No global atomics, no zero fill.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 #include <mutex>
@@ -25,6 +26,49 @@
 #include "pkmom_internal.cuh"
 
 namespace pkmom {
+
+// ------------------------------------------------------------------ checked builds
+namespace {
+#if PKMOM_CHECKED
+__device__ unsigned g_check_word;
+__device__ __forceinline__ bool check_index(long long i, long long n, unsigned code)
+{
+    if (i >= 0 && i < n) return true;
+    atomicOr(&g_check_word, code);
+    return false;
+}
+#endif
+}  // namespace
+
+unsigned take_check_word_assign()
+{
+#if PKMOM_CHECKED
+    unsigned w = 0;
+    if (cudaMemcpyFromSymbol(&w, g_check_word, sizeof w) != cudaSuccess) return 0;
+    if (w) {
+        const unsigned zero = 0;
+        cudaMemcpyToSymbol(g_check_word, &zero, sizeof zero);
+    }
+    return w;
+#else
+    return 0;
+#endif
+}
+
+namespace {
+// One index test that fails on purpose: index 1 against a bound of 1. The failed test
+// records kChkSelf and no access follows it (checked builds; a no-op otherwise).
+__global__ void k_check_selftest(int one)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0 && !PK_IN(one, one, kChkSelf)) return;
+}
+}  // namespace
+
+cudaError_t launch_check_selftest(cudaStream_t s)
+{
+    k_check_selftest<<<1, 32, 0, s>>>(1);
+    return cudaGetLastError();
+}
 namespace {
 
 constexpr int kHistThreads = 256;
@@ -89,10 +133,12 @@ k_hist(const T *__restrict__ x, const T *__restrict__ y, const T *__restrict__ z
         const int64_t j = i * stride;
         const T u0 = mul_rn(x[j], scale), u1 = mul_rn(y[j], scale), u2 = mul_rn(z[j], scale);
         int c0, c1, c2;
-        if (cell_of(u0, ng, c0) & cell_of(u1, ng, c1) & cell_of(u2, ng, c2))
-            atomicAdd(counts + (static_cast<int64_t>(c0) * ng + c1) * nseg + (c2 >> sshift), 1u);
-        else
+        if (cell_of(u0, ng, c0) & cell_of(u1, ng, c1) & cell_of(u2, ng, c2)) {
+            const int64_t key = (static_cast<int64_t>(c0) * ng + c1) * nseg + (c2 >> sshift);
+            if (PK_IN(key, static_cast<int64_t>(ng) * ng * nseg, kChkKey)) atomicAdd(counts + key, 1u);
+        } else {
             *err = 1;
+        }
     };
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += 2 * step) {
         one(i);
@@ -423,7 +469,9 @@ k_scatter(const T *__restrict__ x, const T *__restrict__ y, const T *__restrict_
         int c0, c1, c2;
         if (!(cell_of(u0, ng, c0) & cell_of(u1, ng, c1) & cell_of(u2, ng, c2))) continue;  // reported by k_hist
         const int64_t key = (static_cast<int64_t>(c0) * ng + c1) * nseg + (c2 >> sshift);
+        if (!PK_IN(key, static_cast<int64_t>(ng) * ng * nseg, kChkKey)) continue;
         const uint32_t dst = atomicAdd(cursor + key, 1u);
+        if (!PK_IN(dst, n, kChkRecord)) continue;
         const T m = mass ? mass[i] : T(1);
         Record<T> r;
         r.u = Vec4<T>{u0 - floor(u0), u1 - floor(u1), u2 - floor(u2), pack_cell<T>(c0, c1, c2)};
@@ -724,7 +772,8 @@ k_deposit(const Record<T> *__restrict__ rec, const uint32_t *__restrict__ offset
         const int l1 = l01 % T1, l0 = l01 / T1;
         const int64_t gi = (static_cast<int64_t>(t0 + l0) * ng + (t1 + l1)) * (ng + 2) + t2 + l2;
 #pragma unroll
-        for (int f = 0; f < 4; ++f) grids[f * grid_elems + gi] = acc[f * C::TN + k];
+        if (PK_IN(gi, grid_elems, kChkGrid))
+            for (int f = 0; f < 4; ++f) grids[f * grid_elems + gi] = acc[f * C::TN + k];
     }
 }
 
@@ -959,6 +1008,13 @@ __device__ __forceinline__ void banked_particle(const Record<float> &r, int ng, 
         w[2][k] = static_cast<unsigned>(b2 + k) < static_cast<unsigned>(T2) ? w[2][k] : 0.0f;
     }
     // (the first node may lie below the accumulator, inside the front padding)
+    // the first node where a particle of the tile's reach can have it (cell offset in
+    // [-HL, T + HR) plus the first node's offset from the cell), which FxLayout's padding
+    // covers (fx_pads_cover)
+    constexpr int LO = -HL + bspline_first<M, float>(0.0f), HI = HR - 1 + bspline_first<M, float>(0.5f);
+    if (!PK_IN(b0 - LO, T0 + HI - LO + 1, kChkShared) || !PK_IN(b1 - LO, T1 + HI - LO + 1, kChkShared) ||
+        !PK_IN(b2 - LO, T2 + HI - LO + 1, kChkShared))
+        return;
     const unsigned base = acc_s + 4u * static_cast<unsigned>(b0 * PX + b1 * RW + b2);
     const float q0 = r.q.x * sc0, q1 = r.q.y * sc1, q2 = r.q.z * sc2, q3 = r.q.w * sc3;
     auto row = [&](auto k0c, auto k1c) {
@@ -1000,13 +1056,13 @@ __device__ __forceinline__ void banked_particle(const Record<float> &r, int ng, 
 // order the sort leaves particles of one cell in.
 constexpr int kListRankMax = 128;  // largest bank group whose list entries are reordered
 
-// (16^3-cell and larger tiles: up to 128 registers, as shared memory already holds them to
-// two per SM; 8^3 tiles: 64, for eight per SM)
-template <int M, int T0, int T1, int T2, int NT, int BLR = 0>
-__global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (NT >= 256 ? 2 : 8))
-k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__ offsets,
-             const unsigned *__restrict__ qmax_bits, int ng, int sshift, float *__restrict__ grids, int64_t grid_elems,
-             int list_cap)
+// One tile of the FP32 gather deposit (the body of k_deposit_fx, and of each work item
+// of its persistent batched form k_deposit_fx_batch). The whole CTA takes part; its
+// shared memory is free again when it returns.
+template <int M, int T0, int T1, int T2, int NT, int BLR>
+__device__ __forceinline__ void fx_tile(const Record<float> *__restrict__ rec, const uint32_t *__restrict__ offsets,
+                                        const unsigned *__restrict__ qmax_bits, int ng, int sshift,
+                                        float *__restrict__ grids, int64_t grid_elems, int list_cap, int tile)
 {
     using C = DepositCfg<float, M, T0, T1, T2, NT>;
     using Lay = FxLayout<T0, T1, T2>;
@@ -1024,7 +1080,6 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
     __shared__ unsigned s_rmask[kListRankMax];  // bank groups with more than r entries
 
     const int ntz = ng / T2, nty = ng / T1;
-    int tile = blockIdx.x;
     const int tz = tile % ntz;
     tile /= ntz;
     const int ty = tile % nty;
@@ -1210,6 +1265,7 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
                     for (int k2 = 0; k2 < M; ++k2) {
                         if (li[2][k2] < 0) continue;
                         const float ww = w01 * w[2][k2];
+                        if (!PK_IN(b01 + li[2][k2], TNP, kChkShared)) continue;
                         int *a = acc + b01 + li[2][k2];
                         atomicAdd(a, __float_as_int(fmaf(q0, ww, kMagic)) - kMagicBits);
                         atomicAdd(a + TNP, __float_as_int(fmaf(q1, ww, kMagic)) - kMagicBits);
@@ -1243,6 +1299,7 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
             const int l1 = l01 % T1, l0 = l01 / T1;
             const int64_t gi = (static_cast<int64_t>(t0 + l0) * ng + (t1 + l1)) * (ng + 2) + t2 + l2;
             const int ai = l0 * PX + l1 * RW + l2;
+            if (!PK_IN(gi + 1, grid_elems, kChkGrid) || !PK_IN(ai + 1, TNP, kChkShared)) continue;
 #pragma unroll
             for (int f = 0; f < 4; ++f)
                 *reinterpret_cast<float2 *>(grids + f * grid_elems + gi) =
@@ -1255,9 +1312,74 @@ k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__
             const int l1 = l01 % T1, l0 = l01 / T1;
             const int64_t gi = (static_cast<int64_t>(t0 + l0) * ng + (t1 + l1)) * (ng + 2) + t2 + l2;
             const int ai = l0 * PX + l1 * RW + l2;
+            if (!PK_IN(gi, grid_elems, kChkGrid) || !PK_IN(ai, TNP, kChkShared)) continue;
 #pragma unroll
             for (int f = 0; f < 4; ++f) grids[f * grid_elems + gi] = static_cast<float>(acc[f * TNP + ai]) * inv[f];
         }
+    }
+}
+
+// (16^3-cell and larger tiles: up to 128 registers, as shared memory already holds them to
+// two per SM; 8^3 tiles: 64, for eight per SM)
+template <int M, int T0, int T1, int T2, int NT, int BLR = 0>
+__global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (NT >= 256 ? 2 : 8))
+k_deposit_fx(const Record<float> *__restrict__ rec, const uint32_t *__restrict__ offsets,
+             const unsigned *__restrict__ qmax_bits, int ng, int sshift, float *__restrict__ grids, int64_t grid_elems,
+             int list_cap)
+{
+    fx_tile<M, T0, T1, T2, NT, BLR>(rec, offsets, qmax_bits, ng, sshift, grids, grid_elems, list_cap,
+                                    static_cast<int>(blockIdx.x));
+}
+
+// Persistent form of the gather deposit over the tiles of many catalogues (the batched
+// estimate): each CTA takes the next (catalogue, tile) item from a global counter until
+// none is left. Items are independent (each writes its own tile of its own grids), so
+// nothing waits on another item; the order items are taken in does not change any
+// result. While a tile is deposited the CTA asks L2 to prefetch the key-table rows of
+// the item after it (the rows its range search reads first).
+template <int M, int T0, int T1, int T2, int NT>
+__global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (NT >= 256 ? 2 : 8))
+k_deposit_fx_batch(const FxBatch jobs, unsigned long long *__restrict__ counter)
+{
+    __shared__ long long s_item[2];
+    using C = DepositCfg<float, M, T0, T1, T2, NT>;
+    auto job_of = [&](long long item) {
+        int j = 0;
+        while (j + 1 < jobs.n && jobs.job[j + 1].first_tile <= item) ++j;
+        return j;
+    };
+    auto prefetch_rows = [&](long long item) {
+        if (item >= jobs.total_tiles) return;
+        const FxJob &jb = jobs.job[job_of(item)];
+        const int ng = jb.ng, ntz = ng / T2, nty = ng / T1;
+        int tile = static_cast<int>(item - jb.first_tile);
+        const int tz = tile % ntz;
+        tile /= ntz;
+        const int ty = tile % nty, tx = tile / nty;
+        const int nseg = ng >> jb.sshift;
+        for (int r = threadIdx.x; r < C::R0 * C::R1; r += NT) {
+            int a0 = tx * T0 - C::HL + r / C::R1, a1 = ty * T1 - C::HL + r % C::R1;
+            a0 = a0 < 0 ? a0 + ng : (a0 >= ng ? a0 - ng : a0);
+            a1 = a1 < 0 ? a1 + ng : (a1 >= ng ? a1 - ng : a1);
+            const uint32_t *row = jb.offsets + (static_cast<int64_t>(a0) * ng + a1) * nseg + ((tz * T2) >> jb.sshift);
+            asm volatile("prefetch.L2 [%0];" ::"l"(row));
+        }
+    };
+    if (threadIdx.x == 0) s_item[0] = static_cast<long long>(atomicAdd(counter, 1ull));
+    __syncthreads();
+    long long item = s_item[0];
+    int buf = 0;
+    while (item < jobs.total_tiles) {
+        if (threadIdx.x == 0) s_item[buf ^ 1] = static_cast<long long>(atomicAdd(counter, 1ull));
+        __syncthreads();
+        const long long next = s_item[buf ^ 1];
+        prefetch_rows(next);
+        const FxJob &jb = jobs.job[job_of(item)];
+        fx_tile<M, T0, T1, T2, NT, 0>(jb.rec, jb.offsets, jb.qmax, jb.ng, jb.sshift, jb.grids, jb.grid_elems,
+                                      jb.list_cap, static_cast<int>(item - jb.first_tile));
+        __syncthreads();
+        item = next;
+        buf ^= 1;
     }
 }
 
@@ -1325,15 +1447,15 @@ static_assert(kHomeT - 1 + 3 < kHomeB && 4 * 3 + 6 < kHomeB && kHomeT % 4 == 0 &
 // Halo index of buffer node (bx, by, bz), at least one coordinate in {0, 17, 18}:
 // first the three x planes (19 x 19 each), then the y planes of the inner x range
 // (16 x 19), then the z planes of the inner x, y range (16 x 16).
-__device__ __forceinline__ int home_side(int b) { return b == 0 ? 0 : b - kHomeT; }  // 0, 17, 18 -> 0, 1, 2
-__device__ __forceinline__ int home_unside(int s) { return s == 0 ? 0 : s + kHomeT; }
-__device__ __forceinline__ int home_halo_index(int bx, int by, int bz)
+__host__ __device__ constexpr int home_side(int b) { return b == 0 ? 0 : b - kHomeT; }  // 0, 17, 18 -> 0, 1, 2
+__host__ __device__ constexpr int home_unside(int s) { return s == 0 ? 0 : s + kHomeT; }
+__host__ __device__ constexpr int home_halo_index(int bx, int by, int bz)
 {
     if (bx == 0 || bx > kHomeT) return (home_side(bx) * kHomeB + by) * kHomeB + bz;
     if (by == 0 || by > kHomeT) return 3 * kHomeB * kHomeB + ((bx - 1) * 3 + home_side(by)) * kHomeB + bz;
     return 3 * kHomeB * kHomeB + 3 * kHomeT * kHomeB + ((bx - 1) * kHomeT + (by - 1)) * 3 + home_side(bz);
 }
-__device__ __forceinline__ void home_halo_node(int k, int &bx, int &by, int &bz)
+__host__ __device__ constexpr void home_halo_node(int k, int &bx, int &by, int &bz)
 {
     constexpr int nx = 3 * kHomeB * kHomeB, ny = 3 * kHomeT * kHomeB;
     if (k < nx) {
@@ -1356,6 +1478,22 @@ __device__ __forceinline__ void home_halo_node(int k, int &bx, int &by, int &bz)
     }
 }
 
+// home_halo_node inverts home_halo_index over the 2763 halo nodes, and every node it
+// gives has a coordinate on the halo (0, 17 or 18)
+constexpr bool home_halo_bijective()
+{
+    for (int k = 0; k < kHomeHalo; ++k) {
+        int bx = 0, by = 0, bz = 0;
+        home_halo_node(k, bx, by, bz);
+        const bool inner = bx >= 1 && bx <= kHomeT && by >= 1 && by <= kHomeT && bz >= 1 && bz <= kHomeT;
+        if (inner || bx < 0 || bx >= kHomeB || by < 0 || by >= kHomeB || bz < 0 || bz >= kHomeB ||
+            home_halo_index(bx, by, bz) != k)
+            return false;
+    }
+    return true;
+}
+static_assert(home_halo_bijective(), "the halo scratch layout must be a bijection");
+
 // Shared-memory add without a returned value (the accumulators are read only after a
 // barrier): addr is a shared-window byte address.
 __device__ __forceinline__ void red_shared_add(unsigned addr, int v)
@@ -1376,6 +1514,8 @@ __device__ __forceinline__ void home_particle(int *acc, const Record<float> &r, 
     bspline_weights<4, float>(r.u.y, wy, first);
     bspline_weights<4, float>(r.u.z, wz, first);
     const float q0 = r.q.x * sc0, q1 = r.q.y * sc1, q2 = r.q.z * sc2, q3 = r.q.w * sc3;
+    // its last stencil node (3, 3, 3 from the first) must lie in the node buffer
+    if (!PK_IN((cx + 3) * kHomePX + (cy + 3) * kHomePY + cz + 3, kHomeField, kChkShared)) return;
     // shared-window byte address of the particle's first stencil node
     const unsigned base = static_cast<unsigned>(__cvta_generic_to_shared(acc)) + 4u * (cx * kHomePX + cy * kHomePY + cz);
 #pragma unroll
@@ -1427,6 +1567,8 @@ __device__ __forceinline__ void home_quad(unsigned acc_s, const Record<float> (&
     // buffer index of node (cx - 1 + dx, cy - 1 + dy, 4m - 1 + i) is (cx + dx) PX + (cy + dy) PY + 4m + i.
     // The 4 x 4 node columns are two rolled loops (a short body for the instruction
     // cache); the weights of the current dx and dy are kept in slot 0 by rotating them.
+    // the lane's last node (3, 3 node columns on, z node 4m + 6) must lie in the buffer
+    if (!PK_IN((cx + 3) * kHomePX + (cy + 3) * kHomePY + 4 * m + 6, kHomeField, kChkShared)) return;
     unsigned base = acc_s + 4u * static_cast<unsigned>(cx * kHomePX + cy * kHomePY + 4 * m);
 #pragma unroll 1
     for (int dx = 0; dx < 4; ++dx) {
@@ -1506,6 +1648,7 @@ __device__ __forceinline__ void home_cells_path(const Record<float> *__restrict_
         const uint32_t beg = offsets[key], end = offsets[key + 1];
         if (beg == end) continue;
         const int oa = (cx + dxl) * kHomePX + (cy + dy) * kHomePY + cz + dz, ob = oa + 2 * kHomePX;
+        if (!PK_IN(ob, kHomeField, kChkShared)) continue;
         for (uint32_t i0 = beg; i0 < end; i0 += kCellFlush) {
             int a[2], b[2];
             cell_chunk<F0, 2>(rec, i0, min(end, i0 + kCellFlush), pc, fine, noshift, a, b);
@@ -1579,18 +1722,30 @@ k_deposit_home(const Record<float> *__restrict__ rec, const uint32_t *__restrict
     const float sc0 = s_scale[0], sc1 = s_scale[1], sc2 = s_scale[2], sc3 = s_scale[3];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    // owned nodes to the grid, halo nodes to this tile's scratch; value(f, buffer index)
+    // owned nodes to the grid, halo nodes to this tile's scratch; value(f, buffer index).
+    // Owned rows: eight lanes per (x, y) row, two z nodes each (8-byte stores: the rows
+    // start at even offsets, ng + 2 and the tile corner being even, and the grids are
+    // 16-byte aligned).
     float *h = halo + static_cast<int64_t>(blockIdx.x) * 4 * kHomeHalo;
     auto emit = [&](int f, auto value) {
-        for (int k = threadIdx.x; k < static_cast<int>(kCells); k += kHomeNT) {
-            const int z = k & 15, y = (k >> 4) & 15, x = k >> 8;
-            const int64_t gi = (static_cast<int64_t>(t0 + x) * ng + (t1 + y)) * (ng + 2) + t2 + z;
-            grids[f * grid_elems + gi] = value((x + 1) * kHomePX + (y + 1) * kHomePY + z + 1);
+        float *gf = grids + f * grid_elems;
+#pragma unroll 2
+        for (int pass = 0; pass < kHomeT * kHomeT * 8 / kHomeNT; ++pass) {
+            const int rowi = pass * (kHomeNT / 8) + (threadIdx.x >> 3), zp = 2 * (threadIdx.x & 7);
+            const int x = rowi >> 4, y = rowi & 15;
+            const int ab = (x + 1) * kHomePX + (y + 1) * kHomePY + zp + 1;
+            const int64_t gi = (static_cast<int64_t>(t0 + x) * ng + (t1 + y)) * (ng + 2) + t2 + zp;
+            if (PK_IN(gi + 1, grid_elems, kChkGrid) && PK_IN(ab + 1, kHomeField, kChkShared))
+                *reinterpret_cast<float2 *>(gf + gi) = make_float2(value(ab), value(ab + 1));
         }
         for (int k = threadIdx.x; k < kHomeHalo; k += kHomeNT) {
             int bx, by, bz;
             home_halo_node(k, bx, by, bz);
-            h[f * kHomeHalo + k] = value(bx * kHomePX + by * kHomePY + bz);
+            const int ai = bx * kHomePX + by * kHomePY + bz;
+            if (PK_IN(static_cast<int64_t>(blockIdx.x) * 4 * kHomeHalo + f * kHomeHalo + k,
+                      static_cast<int64_t>(gridDim.x) * 4 * kHomeHalo, kChkHalo) &&
+                PK_IN(ai, kHomeField, kChkShared))
+                h[f * kHomeHalo + k] = value(ai);
         }
     };
 
@@ -1731,6 +1886,7 @@ k_home_fixup(const float *__restrict__ halo, int ng, float *__restrict__ grids, 
             z = home_face(r % 3);
         }
         const int64_t gi = (static_cast<int64_t>(tx * kHomeT + x) * ng + (ty * kHomeT + y)) * (ng + 2) + tz * kHomeT + z;
+        if (!PK_IN(gi, grid_elems, kChkGrid)) continue;
         float v[4];
 #pragma unroll
         for (int f = 0; f < 4; ++f) v[f] = grids[f * grid_elems + gi];
@@ -1742,6 +1898,9 @@ k_home_fixup(const float *__restrict__ halo, int ng, float *__restrict__ grids, 
             if (((c & 4) && !sx) || ((c & 2) && !sy) || ((c & 1) && !sz)) continue;
             const int nb = (wrap(tx + dx) * nt + wrap(ty + dy)) * nt + wrap(tz + dz);
             const int hi = home_halo_index(x - kHomeT * dx + 1, y - kHomeT * dy + 1, z - kHomeT * dz + 1);
+            if (!PK_IN(static_cast<int64_t>(nb) * 4 * kHomeHalo + 3 * kHomeHalo + hi,
+                       static_cast<int64_t>(gridDim.x) * 4 * kHomeHalo, kChkHalo))
+                continue;
             const float *hp = halo + static_cast<int64_t>(nb) * 4 * kHomeHalo + hi;
 #pragma unroll
             for (int f = 0; f < 4; ++f) v[f] += hp[f * kHomeHalo];
@@ -2009,6 +2168,52 @@ cudaError_t launch_scatter(const pkmom_catalog &cat, const AssignPlan &pl, doubl
                                                  tp<double>(cat.mass), cat.stride, cat.n, partials, qmax);
     }
     st.launches++;
+    st.launches++;
+    return cudaGetLastError();
+}
+
+bool batchable_deposit(const AssignPlan &pl)
+{
+    return pl.prec == PKMOM_F32 && pl.order == 4 && pl.bl_radius == 0 && pl.tile == 0;
+}
+
+FxJob deposit_job(const AssignPlan &pl, void *scratch, void *grids)
+{
+    char *sc = static_cast<char *>(scratch);
+    FxJob j{};
+    j.rec = reinterpret_cast<const Record<float> *>(sc + pl.off_records);
+    j.offsets = key_table(pl, scratch) - 1;
+    j.qmax = reinterpret_cast<const unsigned *>(sc + pl.off_qmax);
+    j.grids = static_cast<float *>(grids);
+    j.grid_elems = static_cast<int64_t>(pl.ng) * pl.ng * (pl.ng + 2);
+    j.ng = pl.ng;
+    j.sshift = pl.sshift;
+    j.list_cap = pl.list_cap;
+    return j;
+}
+
+cudaError_t launch_deposit_batch(FxBatch &batch, unsigned long long *counter, int num_sms, cudaStream_t s,
+                                 LaunchStats &st)
+{
+    constexpr int T = 16, NT = 256;
+    auto kern = k_deposit_fx_batch<4, T, T, T, NT>;
+    long long first = 0;
+    int cap = 0;
+    for (int k = 0; k < batch.n; ++k) {
+        batch.job[k].first_tile = first;
+        first += static_cast<long long>(batch.job[k].ng / T) * (batch.job[k].ng / T) * (batch.job[k].ng / T);
+        cap = std::max(cap, batch.job[k].list_cap);
+    }
+    batch.total_tiles = first;
+    if (first == 0) return cudaSuccess;
+    const size_t smem = FxLayout<T, T, T>::bytes(cap);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem)) != cudaSuccess) return e;
+    const long long ctas = std::min<long long>(first, static_cast<long long>(std::max(1, per_sm)) * num_sms);
+    if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    kern<<<static_cast<unsigned>(ctas), NT, smem, s>>>(batch, counter);
     st.launches++;
     return cudaGetLastError();
 }

@@ -7,7 +7,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
+#include <deque>
 #include <string>
 #include <vector>
 
@@ -33,7 +35,9 @@ struct pkmom_ctx {
     int *d_err = nullptr;  // device-side data error word
     LaunchStats st;
     std::vector<PlanEntry> plans;
-    std::vector<SpectraTables> tables;
+    // a deque: the addresses of cached tables stay valid while more are added (a batch
+    // holds pointers to several of them at once)
+    std::deque<SpectraTables> tables;
     // buffers owned for pkmom_estimate / pkmom_estimate_host
     void *grids = nullptr;
     size_t grids_bytes = 0;
@@ -369,7 +373,8 @@ pkmom_status stage_catalog(pkmom_ctx *ctx, const pkmom_catalog &cat, size_t elem
     return PKMOM_OK;
 }
 
-// Returns (and clears) a device-side data error latched by the context's kernels.
+// Returns (and clears) a device-side data error latched by the context's kernels, and in
+// checked builds a failed index test of any kernel on this device.
 pkmom_status check_error_word(pkmom_ctx *ctx)
 {
     int flag = 0;
@@ -377,6 +382,14 @@ pkmom_status check_error_word(pkmom_ctx *ctx)
     if (flag) {
         PK_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)), "clear error word");
         return fail(ctx, PKMOM_EDATA, "catalogue held non-finite or out-of-range positions (|x ng/L| >= 2^30)");
+    }
+    if (PKMOM_CHECKED) {
+        const unsigned w = take_check_word_assign() | take_check_word_spectra();
+        if (w) {
+            char buf[96];
+            std::snprintf(buf, sizeof buf, "index out of range in the checked build (test codes 0x%x)", w);
+            return fail(ctx, PKMOM_EDATA, buf);
+        }
     }
     return PKMOM_OK;
 }
@@ -501,6 +514,8 @@ pkmom_status pkmom_assign(pkmom_ctx *ctx, const pkmom_catalog *cat, const pkmom_
     if ((s = check_params(ctx, p)) != PKMOM_OK) return s;
     if ((s = check_catalog(ctx, cat, p)) != PKMOM_OK) return s;
     if (!grids || !moments_dev || !scratch) return fail(ctx, PKMOM_EINVAL, "null grids, moments or scratch");
+    if (reinterpret_cast<uintptr_t>(grids) % 16 || reinterpret_cast<uintptr_t>(scratch) % 16)
+        return fail(ctx, PKMOM_EINVAL, "grids and scratch must be 16-byte aligned");
     PK_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
     const AssignPlan pl = plan_assign(*p, cat->n, ctx->num_sms, ctx->tune_tile, ctx->tune_list_cap);
     if (scratch_bytes < pl.total) return fail(ctx, PKMOM_ESCRATCH, "scratch smaller than pkmom_assign_scratch_bytes");
@@ -722,6 +737,142 @@ pkmom_status pkmom_wait(pkmom_ctx *ctx, int64_t ticket)
     return check_error_word(ctx);
 }
 
+namespace {
+struct BatchLayout {
+    size_t counter = 0, total = 0;
+    std::vector<size_t> partials, sums;  // offsets per item (FP32 items), else unused
+};
+BatchLayout batch_layout(int n, const pkmom_batch_item *items)
+{
+    BatchLayout L;
+    size_t off = align_up(sizeof(unsigned long long));
+    L.partials.assign(n, 0);
+    L.sums.assign(n, 0);
+    for (int k = 0; k < n; ++k) {
+        const pkmom_params &p = items[k].p;
+        if (p.precision != PKMOM_F32) continue;
+        L.partials[k] = off;
+        off = align_up(off + size_t(p.ng) * p.nbins * kBinVals * sizeof(double));
+        L.sums[k] = off;
+        off = align_up(off + size_t(kBinVals) * p.nbins * sizeof(double));
+    }
+    L.total = off;
+    return L;
+}
+}  // namespace
+
+size_t pkmom_batch_work_bytes(int n, const pkmom_batch_item *items)
+{
+    if (n < 1 || n > PKMOM_BATCH_MAX || !items) return 0;
+    for (int k = 0; k < n; ++k)
+        if (check_params(nullptr, &items[k].p) != PKMOM_OK) return 0;
+    return batch_layout(n, items).total;
+}
+
+pkmom_status pkmom_estimate_batch(pkmom_ctx *ctx, int n, const pkmom_batch_item *items, void *work,
+                                  size_t work_bytes, void *stream)
+{
+    if (!ctx) return PKMOM_EINVAL;
+    if (n < 1 || n > PKMOM_BATCH_MAX || !items) return fail(ctx, PKMOM_EINVAL, "need 1..PKMOM_BATCH_MAX items");
+    if (!work || reinterpret_cast<uintptr_t>(work) % 16) return fail(ctx, PKMOM_EINVAL, "work must be 16-byte aligned");
+    pkmom_status s;
+    std::vector<AssignPlan> plans(n);
+    std::vector<const SpectraTables *> tabs(n, nullptr);
+    PK_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t st = as_stream(stream);
+    for (int k = 0; k < n; ++k) {
+        const pkmom_batch_item &it = items[k];
+        if ((s = check_params(ctx, &it.p)) != PKMOM_OK) return s;
+        if ((s = check_catalog(ctx, &it.cat, &it.p)) != PKMOM_OK) return s;
+        if (!it.grids || !it.moments_dev || !it.scratch || !it.out_dev)
+            return fail(ctx, PKMOM_EINVAL, "null grids, moments, scratch or output in a batch item");
+        if (reinterpret_cast<uintptr_t>(it.grids) % 16 || reinterpret_cast<uintptr_t>(it.scratch) % 16)
+            return fail(ctx, PKMOM_EINVAL, "grids and scratch must be 16-byte aligned");
+        if (it.deposit_tile >= deposit_tile_count() || it.list_cap > 8192)
+            return fail(ctx, PKMOM_EINVAL, "bad tuning values in a batch item");
+        plans[k] = plan_assign(it.p, it.cat.n, ctx->num_sms, it.deposit_tile < 0 ? -1 : it.deposit_tile,
+                               it.list_cap < 0 ? -1 : it.list_cap);
+        if (it.scratch_bytes < plans[k].total)
+            return fail(ctx, PKMOM_ESCRATCH, "scratch of a batch item smaller than its assignment needs");
+        cufftHandle h;
+        if ((s = get_plan(ctx, it.p.ng, it.p.precision, &h)) != PKMOM_OK) return s;
+        if ((s = get_tables(ctx, it.p, st, &tabs[k])) != PKMOM_OK) return s;
+    }
+    const BatchLayout L = batch_layout(n, items);
+    if (work_bytes < L.total) return fail(ctx, PKMOM_ESCRATCH, "work buffer smaller than pkmom_batch_work_bytes");
+    char *wk = static_cast<char *>(work);
+    auto *counter = reinterpret_cast<unsigned long long *>(wk + L.counter);
+    {
+        StageTimer t(ctx, PKMOM_STAGE_HIST, st);
+        for (int k = 0; k < n; ++k)
+            PK_CUDA(launch_hist_moments(items[k].cat, plans[k], items[k].p.box_L, items[k].scratch, ctx->d_err, st,
+                                        ctx->st),
+                    "histogram");
+    }
+    {
+        StageTimer t(ctx, PKMOM_STAGE_SCAN, st);
+        for (int k = 0; k < n; ++k) PK_CUDA(launch_scan(plans[k], items[k].scratch, st, ctx->st), "scan");
+    }
+    {
+        StageTimer t(ctx, PKMOM_STAGE_SCATTER, st);
+        for (int k = 0; k < n; ++k) {
+            PK_CUDA(launch_scatter(items[k].cat, plans[k], items[k].p.box_L, items[k].scratch, st, ctx->st),
+                    "scatter and moments");
+            PK_CUDA(launch_moments_final(plans[k], items[k].cat.n, items[k].scratch,
+                                         static_cast<double *>(items[k].moments_dev), st, ctx->st),
+                    "moments");
+        }
+    }
+    {
+        StageTimer t(ctx, PKMOM_STAGE_DEPOSIT, st);
+        FxBatch fb{};
+        for (int k = 0; k < n; ++k) {
+            if (batchable_deposit(plans[k])) fb.job[fb.n++] = deposit_job(plans[k], items[k].scratch, items[k].grids);
+            else PK_CUDA(launch_deposit(plans[k], items[k].scratch, items[k].grids, st, ctx->st), "deposit");
+        }
+        if (fb.n) PK_CUDA(launch_deposit_batch(fb, counter, ctx->num_sms, st, ctx->st), "batched deposit");
+    }
+    for (int k = 0; k < n; ++k)
+        if ((s = pkmom_fft(ctx, &items[k].p, items[k].grids, stream)) != PKMOM_OK) return s;
+    {
+        StageTimer t(ctx, PKMOM_STAGE_BIN, st);
+        BinBatch bb{};
+        std::vector<const SpectraTables *> btabs;
+        std::vector<const pkmom_params *> bpar;
+        std::vector<double *> bsums, bout;
+        for (int k = 0; k < n; ++k) {
+            const pkmom_batch_item &it = items[k];
+            if (it.p.precision != PKMOM_F32) {
+                PK_CUDA(launch_bin_shells(*tabs[k], it.grids, static_cast<const double *>(it.moments_dev), st,
+                                          ctx->st),
+                        "binning");
+                PK_CUDA(launch_finalize(*tabs[k], it.p, static_cast<const double *>(it.moments_dev), it.out_dev, st,
+                                        ctx->st, true),
+                        "finalize");
+                continue;
+            }
+            BinJob &j = bb.job[bb.n++];
+            j.grids = it.grids;
+            j.mom = static_cast<const double *>(it.moments_dev);
+            j.thresh = tabs[k]->thresh;
+            j.gf = static_cast<const float *>(tabs[k]->g_full);
+            j.gh = static_cast<const float *>(tabs[k]->g_half);
+            j.partials = reinterpret_cast<double *>(wk + L.partials[k]);
+            j.ng = it.p.ng;
+            j.nbins = it.p.nbins;
+            btabs.push_back(tabs[k]);
+            bpar.push_back(&it.p);
+            bsums.push_back(reinterpret_cast<double *>(wk + L.sums[k]));
+            bout.push_back(it.out_dev);
+        }
+        if (bb.n)
+            PK_CUDA(launch_bin_batch(bb, btabs.data(), bpar.data(), bsums.data(), bout.data(), ctx->num_sms, st,
+                                     ctx->st),
+                    "batched binning");
+    }
+    return PKMOM_OK;
+}
+
 pkmom_status pkmom_sync(pkmom_ctx *ctx, void *stream)
 {
     if (!ctx) return PKMOM_EINVAL;
@@ -760,6 +911,18 @@ pkmom_status pkmom_timing_read(pkmom_ctx *ctx, double ms[PKMOM_NSTAGES], int64_t
 }
 
 int64_t pkmom_kernel_launches(const pkmom_ctx *ctx) { return ctx ? ctx->st.launches : 0; }
+
+int pkmom_checked(void) { return PKMOM_CHECKED; }
+
+pkmom_status pkmom_checked_selftest(pkmom_ctx *ctx, void *stream)
+{
+    if (!ctx) return PKMOM_EINVAL;
+    if (!PKMOM_CHECKED) return fail(ctx, PKMOM_EUNSUPPORTED, "not a checked build");
+    PK_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    PK_CUDA(launch_check_selftest(as_stream(stream)), "self-test");
+    ctx->st.launches++;
+    return PKMOM_OK;
+}
 
 size_t pkmom_context_bytes(const pkmom_ctx *ctx)
 {

@@ -6,7 +6,38 @@
 
 #include "../../include/pkmom.h"
 
+// Checked builds (compiled with -DPKMOM_CHECKED=1 into libpkmom_checked.so): every
+// grid, halo, shared-buffer, sort-key, record and bin index is tested before its access;
+// a failed test sets its code in the translation unit's device error word (check_index,
+// defined in each .cu) and the access is skipped, so nothing is read or written out of
+// range. pkmom_sync reports a set word as PKMOM_EDATA. In unchecked builds PK_IN is true.
+#ifndef PKMOM_CHECKED
+#define PKMOM_CHECKED 0
+#endif
+#if PKMOM_CHECKED
+#define PK_IN(i, n, code) check_index(static_cast<long long>(i), static_cast<long long>(n), (code))
+#else
+#define PK_IN(i, n, code) true
+#endif
+
 namespace pkmom {
+
+// Codes of the checked build's index tests (bits of the device error word).
+enum : unsigned {
+    kChkKey = 1u,        // sort key beyond the key table
+    kChkRecord = 2u,     // record slot beyond the catalogue
+    kChkGrid = 4u,       // grid element beyond a grid
+    kChkShared = 8u,     // node beyond a shared accumulator
+    kChkHalo = 16u,      // halo scratch element beyond the scratch
+    kChkMode = 32u,      // Fourier mode beyond a half spectrum
+    kChkBin = 64u,       // shell or item beyond the partial sums
+    kChkSelf = 1u << 31  // the self-test's deliberate failed test (no access follows it)
+};
+// Host: reads and clears the error word of assign.cu / spectra.cu (0 in unchecked builds).
+unsigned take_check_word_assign();
+unsigned take_check_word_spectra();
+// Host: launches a kernel whose one index test fails on purpose (checked builds).
+cudaError_t launch_check_selftest(cudaStream_t s);
 
 // Number of doubles in a device pkmom_moments.
 constexpr int kMomentWords = 16;
@@ -44,6 +75,42 @@ struct LaunchStats {
     int64_t launches = 0;
 };
 
+// One catalogue of a persistent batched gather deposit (16^3 tiles, cubic order, FP32):
+// its sorted records, key table, largest |q| per field, grids and its first global tile.
+struct FxJob {
+    const Record<float> *rec;
+    const uint32_t *offsets;
+    const unsigned *qmax;
+    float *grids;
+    int64_t grid_elems;
+    long long first_tile;
+    int ng, sshift, list_cap, pad;
+};
+// The jobs of one launch, passed by value as the kernel's parameter (under 8 KB).
+constexpr int kBatchMax = 128;
+struct FxBatch {
+    FxJob job[kBatchMax];
+    int n;
+    long long total_tiles;
+};
+
+// One catalogue of a persistent batched binning (FP32 grids): its transformed grids,
+// moments, shell tables and its own per-item partial sums; its first global item.
+struct BinJob {
+    const void *grids;
+    const double *mom;
+    const int *thresh;
+    const float *gf, *gh;
+    double *partials;
+    long long first_item;
+    int ng, nbins;
+};
+struct BinBatch {
+    BinJob job[kBatchMax];
+    int n;
+    long long total_items;
+};
+
 // ---------------------------------------------------------------- assign.cu
 cudaError_t launch_hist_moments(const pkmom_catalog &cat, const AssignPlan &pl, double box_L, void *scratch,
                                 int *err_flag, cudaStream_t s, LaunchStats &st);
@@ -53,6 +120,13 @@ cudaError_t launch_scan(const AssignPlan &pl, void *scratch, cudaStream_t s, Lau
 cudaError_t launch_scatter(const pkmom_catalog &cat, const AssignPlan &pl, double box_L, void *scratch,
                            cudaStream_t s, LaunchStats &st);
 cudaError_t launch_deposit(const AssignPlan &pl, void *scratch, void *grids, cudaStream_t s, LaunchStats &st);
+// Whether launch_deposit_batch can take this assignment (16^3 gather tiles, cubic, FP32,
+// exact BL kernel), and its FxJob (scratch and grids of that catalogue).
+bool batchable_deposit(const AssignPlan &pl);
+FxJob deposit_job(const AssignPlan &pl, void *scratch, void *grids);
+// One persistent launch over the tiles of jobs[0 .. batch.n); counter: one device word.
+cudaError_t launch_deposit_batch(FxBatch &batch, unsigned long long *counter, int num_sms, cudaStream_t s,
+                                 LaunchStats &st);
 // bytes of the key table (counts, then offsets) for nkeys sort keys
 size_t key_table_bytes(int64_t nkeys);
 // Tile shapes the deposit kernel is instantiated for (x, y, z nodes).
@@ -89,6 +163,12 @@ cudaError_t launch_bin(const SpectraTables &t, const void *grids, const double *
                        LaunchStats &st);
 cudaError_t launch_bin_shells(const SpectraTables &t, const void *grids, const double *moments_dev, cudaStream_t s,
                               LaunchStats &st);
+// Persistent binning over the (slab, shell) items of many FP32 catalogues, each into its
+// own partials (ng * nbins * kBinVals doubles), then per catalogue the fixed-order
+// reduction into sums[kBinVals * nbins] (sums_of[k]) and the finalisation into out[k].
+cudaError_t launch_bin_batch(BinBatch &batch, const SpectraTables *const *tables, const pkmom_params *const *params,
+                             double *const *sums_of, double *const *out, int num_sms, cudaStream_t s,
+                             LaunchStats &st);
 // sums_ready: the shell sums were already reduced (by launch_bin_shells); otherwise the
 // per-block partials of launch_bin are reduced first
 cudaError_t launch_finalize(const SpectraTables &t, const pkmom_params &p, const double *moments_dev,

@@ -20,6 +20,7 @@
 // sum w |n|, sum w h, sum w h n n^T) are built once per grid/shell layout by
 // k_mode_sums in FP64. k_finalize subtracts the shot noise at the shell level in
 // FP64, where the cancellation against large shot noise is harmless.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -27,6 +28,34 @@
 #include "pkmom_internal.cuh"
 
 namespace pkmom {
+
+// ------------------------------------------------------------------ checked builds
+namespace {
+#if PKMOM_CHECKED
+__device__ unsigned g_check_word;
+__device__ __forceinline__ bool check_index(long long i, long long n, unsigned code)
+{
+    if (i >= 0 && i < n) return true;
+    atomicOr(&g_check_word, code);
+    return false;
+}
+#endif
+}  // namespace
+
+unsigned take_check_word_spectra()
+{
+#if PKMOM_CHECKED
+    unsigned w = 0;
+    if (cudaMemcpyFromSymbol(&w, g_check_word, sizeof w) != cudaSuccess) return 0;
+    if (w) {
+        const unsigned zero = 0;
+        cudaMemcpyToSymbol(g_check_word, &zero, sizeof zero);
+    }
+    return w;
+#else
+    return 0;
+#endif
+}
 namespace {
 
 template <typename T> struct Cx { T x, y; };
@@ -184,6 +213,112 @@ __device__ __forceinline__ int isqrt_floor(int x)
 // values are summed with Kahan-compensated adds in the grid precision; one warp
 // reduction per item (float pairs for FP32) writes partials[item][kBinVals] in FP64, and
 // k_reduce_items adds the items of each shell in a fixed order.
+// Per-warp staging of the rows of one item (k_bin_shells, k_bin_batch).
+template <typename T>
+struct BinWarpStage {
+    int lo[32], pre[32], n1[32];
+    int64_t row[32];
+    T g[32];
+};
+
+// One item (n0 = slab i0, shell b) of the shell-major binning, by one warp: writes
+// partials[item][kBinVals] (item = i0 * nbins + b).
+template <typename T>
+__device__ __forceinline__ void bin_item(const Cx<T> *__restrict__ F, int64_t gstride, int ng, int nbins,
+                                         const int *__restrict__ thresh, const T *__restrict__ gf,
+                                         const T *__restrict__ gh, T vb0, T vb1, T vb2, double *__restrict__ partials,
+                                         int item, BinWarpStage<T> &st)
+{
+    const int nh = ng / 2 + 1;
+    const int lane = threadIdx.x & 31;
+    if (!PK_IN(item, static_cast<int64_t>(ng) * nbins, kChkBin)) return;  // warp-uniform
+    const int b = item % nbins;
+    const int i0 = item / nbins;
+    const int n0 = i0 < ng / 2 ? i0 : i0 - ng;
+    const int lo2 = thresh[b], hi2 = thresh[b + 1];  // lo2 <= |n|^2 < hi2
+    T s[kBinVals], c[kBinVals];
+#pragma unroll
+    for (int k = 0; k < kBinVals; ++k) s[k] = T(0), c[k] = T(0);
+    const int rem = hi2 - 1 - n0 * n0;
+    if (hi2 > lo2 && rem >= 0) {
+        const int R1 = isqrt_floor(rem);
+        const int n1lo = max(-ng / 2, -R1), n1hi = min(ng / 2 - 1, R1);
+        const T g0 = gf[i0];
+        for (int r0 = n1lo; r0 <= n1hi; r0 += 32) {
+            const int n1 = r0 + lane;
+            const bool row = n1 <= n1hi;
+            int l_lo = 0, len = 0;
+            if (row) {
+                const int r2 = n0 * n0 + n1 * n1;
+                const int top = hi2 - 1 - r2;  // l^2 <= top
+                if (top >= 0) {
+                    const int lh = min(isqrt_floor(top), nh - 1);
+                    const int need = lo2 - r2;  // l^2 >= need
+                    const int ll = need <= 0 ? 0 : isqrt_floor(need - 1) + 1;
+                    if (lh >= ll) l_lo = ll, len = lh - ll + 1;
+                }
+            }
+            int inc = len;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, inc, d);
+                if (lane >= d) inc += t;
+            }
+            const int total = __shfl_sync(0xffffffffu, inc, 31);
+            if (total == 0) continue;
+            const int i1 = row ? (n1 < 0 ? n1 + ng : n1) : 0;
+            st.lo[lane] = l_lo;
+            st.pre[lane] = inc - len;
+            st.n1[lane] = n1;
+            st.row[lane] = (static_cast<int64_t>(i0) * ng + i1) * nh;
+            st.g[lane] = row ? g0 * gf[i1] : T(0);
+            __syncwarp();
+            for (int m = lane; m < total; m += 32) {
+                // the row holding the m-th mode: the last row starting at or before m
+                // (an empty row starts where the next one does, which is then taken)
+                int j = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (st.pre[j + step] <= m) j += step;
+                const int l = st.lo[j] + (m - st.pre[j]);
+                const int64_t mi = st.row[j] + l;
+                if (!PK_IN(mi, gstride, kChkMode) || !PK_IN(l, nh, kChkMode)) continue;
+                const T g = st.g[j] * gh[l] * ((l == 0 || l == nh - 1) ? T(1) : T(2));
+                const Cx<T> d = F[mi], p0 = F[gstride + mi], p1 = F[2 * gstride + mi], p2 = F[3 * gstride + mi];
+                const T fn0 = static_cast<T>(n0), fn1 = static_cast<T>(st.n1[j]), fn2 = static_cast<T>(l);
+                const T kr = fn0 * p0.x + fn1 * p1.x + fn2 * p2.x;
+                const T ki = fn0 * p0.y + fn1 * p1.y + fn2 * p2.y;
+                const Cx<T> q0{p0.x - vb0 * d.x, p0.y - vb0 * d.y};
+                const Cx<T> q1{p1.x - vb1 * d.x, p1.y - vb1 * d.y};
+                const Cx<T> q2{p2.x - vb2 * d.x, p2.y - vb2 * d.y};
+                const T jr = fn0 * q0.x + fn1 * q1.x + fn2 * q2.x;
+                const T ji = fn0 * q0.y + fn1 * q1.y + fn2 * q2.y;
+                T v[kBinVals];
+                v[0] = g * (d.x * d.x + d.y * d.y);
+                v[1] = g * (p0.x * p0.x + p0.y * p0.y + p1.x * p1.x + p1.y * p1.y + p2.x * p2.x + p2.y * p2.y);
+                v[2] = g * (kr * kr + ki * ki);
+                v[3] = g * (d.x * ki - d.y * kr);  // Im(conj(F_d) * (n.F_p))
+                v[4] = g * (q0.x * q0.x + q0.y * q0.y + q1.x * q1.x + q1.y * q1.y + q2.x * q2.x + q2.y * q2.y);
+                v[5] = g * (jr * jr + ji * ji);
+                v[6] = g * (d.x * ji - d.y * jr);
+#pragma unroll
+                for (int k = 0; k < kBinVals; ++k) {  // Kahan: s - c carries the sum
+                    const T y = v[k] - c[k];
+                    const T t = s[k] + y;
+                    c[k] = (t - s[k]) - y;
+                    s[k] = t;
+                }
+            }
+            __syncwarp();
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kBinVals; ++k) {
+        const double dsum = warp_sum_pair(s[k], -c[k]);
+        if (lane == 0) partials[static_cast<int64_t>(item) * kBinVals + k] = dsum;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kBinThreads, sizeof(T) == 4 ? 4 : 2)
 k_bin_shells(const Cx<T> *__restrict__ F, int64_t gstride, int ng, int nbins, const int *__restrict__ thresh,
@@ -191,100 +326,37 @@ k_bin_shells(const Cx<T> *__restrict__ F, int64_t gstride, int ng, int nbins, co
              double *__restrict__ partials)
 {
     constexpr int NW = kBinThreads / 32;
-    __shared__ int s_lo[NW][32], s_pre[NW][32], s_n1[NW][32];
-    __shared__ int64_t s_row[NW][32];
-    __shared__ T s_g[NW][32];
-    const int nh = ng / 2 + 1;
+    __shared__ BinWarpStage<T> s_st[NW];
     const double Mtot = mom[0];
     const T vb0 = static_cast<T>(mom[2] / Mtot), vb1 = static_cast<T>(mom[3] / Mtot), vb2 = static_cast<T>(mom[4] / Mtot);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int w = threadIdx.x >> 5;
     const int nwarps = gridDim.x * NW;
     const int nitems = ng * nbins;
-    for (int item = blockIdx.x * NW + w; item < nitems; item += nwarps) {
-        const int b = item % nbins;
-        const int i0 = item / nbins;
-        const int n0 = i0 < ng / 2 ? i0 : i0 - ng;
-        const int lo2 = thresh[b], hi2 = thresh[b + 1];  // lo2 <= |n|^2 < hi2
-        T s[kBinVals], c[kBinVals];
-#pragma unroll
-        for (int k = 0; k < kBinVals; ++k) s[k] = T(0), c[k] = T(0);
-        const int rem = hi2 - 1 - n0 * n0;
-        if (hi2 > lo2 && rem >= 0) {
-            const int R1 = isqrt_floor(rem);
-            const int n1lo = max(-ng / 2, -R1), n1hi = min(ng / 2 - 1, R1);
-            const T g0 = gf[i0];
-            for (int r0 = n1lo; r0 <= n1hi; r0 += 32) {
-                const int n1 = r0 + lane;
-                const bool row = n1 <= n1hi;
-                int l_lo = 0, len = 0;
-                if (row) {
-                    const int r2 = n0 * n0 + n1 * n1;
-                    const int top = hi2 - 1 - r2;  // l^2 <= top
-                    if (top >= 0) {
-                        const int lh = min(isqrt_floor(top), nh - 1);
-                        const int need = lo2 - r2;  // l^2 >= need
-                        const int ll = need <= 0 ? 0 : isqrt_floor(need - 1) + 1;
-                        if (lh >= ll) l_lo = ll, len = lh - ll + 1;
-                    }
-                }
-                int inc = len;
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const int t = __shfl_up_sync(0xffffffffu, inc, d);
-                    if (lane >= d) inc += t;
-                }
-                const int total = __shfl_sync(0xffffffffu, inc, 31);
-                if (total == 0) continue;
-                const int i1 = row ? (n1 < 0 ? n1 + ng : n1) : 0;
-                s_lo[w][lane] = l_lo;
-                s_pre[w][lane] = inc - len;
-                s_n1[w][lane] = n1;
-                s_row[w][lane] = (static_cast<int64_t>(i0) * ng + i1) * nh;
-                s_g[w][lane] = row ? g0 * gf[i1] : T(0);
-                __syncwarp();
-                for (int m = lane; m < total; m += 32) {
-                    // the row holding the m-th mode: the last row starting at or before m
-                    // (an empty row starts where the next one does, which is then taken)
-                    int j = 0;
-#pragma unroll
-                    for (int step = 16; step > 0; step >>= 1)
-                        if (s_pre[w][j + step] <= m) j += step;
-                    const int l = s_lo[w][j] + (m - s_pre[w][j]);
-                    const int64_t mi = s_row[w][j] + l;
-                    const T g = s_g[w][j] * gh[l] * ((l == 0 || l == nh - 1) ? T(1) : T(2));
-                    const Cx<T> d = F[mi], p0 = F[gstride + mi], p1 = F[2 * gstride + mi], p2 = F[3 * gstride + mi];
-                    const T fn0 = static_cast<T>(n0), fn1 = static_cast<T>(s_n1[w][j]), fn2 = static_cast<T>(l);
-                    const T kr = fn0 * p0.x + fn1 * p1.x + fn2 * p2.x;
-                    const T ki = fn0 * p0.y + fn1 * p1.y + fn2 * p2.y;
-                    const Cx<T> q0{p0.x - vb0 * d.x, p0.y - vb0 * d.y};
-                    const Cx<T> q1{p1.x - vb1 * d.x, p1.y - vb1 * d.y};
-                    const Cx<T> q2{p2.x - vb2 * d.x, p2.y - vb2 * d.y};
-                    const T jr = fn0 * q0.x + fn1 * q1.x + fn2 * q2.x;
-                    const T ji = fn0 * q0.y + fn1 * q1.y + fn2 * q2.y;
-                    T v[kBinVals];
-                    v[0] = g * (d.x * d.x + d.y * d.y);
-                    v[1] = g * (p0.x * p0.x + p0.y * p0.y + p1.x * p1.x + p1.y * p1.y + p2.x * p2.x + p2.y * p2.y);
-                    v[2] = g * (kr * kr + ki * ki);
-                    v[3] = g * (d.x * ki - d.y * kr);  // Im(conj(F_d) * (n.F_p))
-                    v[4] = g * (q0.x * q0.x + q0.y * q0.y + q1.x * q1.x + q1.y * q1.y + q2.x * q2.x + q2.y * q2.y);
-                    v[5] = g * (jr * jr + ji * ji);
-                    v[6] = g * (d.x * ji - d.y * jr);
-#pragma unroll
-                    for (int k = 0; k < kBinVals; ++k) {  // Kahan: s - c carries the sum
-                        const T y = v[k] - c[k];
-                        const T t = s[k] + y;
-                        c[k] = (t - s[k]) - y;
-                        s[k] = t;
-                    }
-                }
-                __syncwarp();
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < kBinVals; ++k) {
-            const double dsum = warp_sum_pair(s[k], -c[k]);
-            if (lane == 0) partials[static_cast<int64_t>(item) * kBinVals + k] = dsum;
-        }
+    for (int item = blockIdx.x * NW + w; item < nitems; item += nwarps)
+        bin_item<T>(F, gstride, ng, nbins, thresh, gf, gh, vb0, vb1, vb2, partials, item, s_st[w]);
+}
+
+// Persistent form over the items of many FP32 catalogues (the batched estimate): warp
+// k of the grid takes the global items k, k + (warps), ...; each item is written to its
+// own catalogue's partials, so the results do not depend on which warp took it.
+__global__ void __launch_bounds__(kBinThreads, 4)
+k_bin_batch(const BinBatch jobs)
+{
+    constexpr int NW = kBinThreads / 32;
+    __shared__ BinWarpStage<float> s_st[NW];
+    const int w = threadIdx.x >> 5;
+    const long long nwarps = static_cast<long long>(gridDim.x) * NW;
+    int j = 0;
+    for (long long item = static_cast<long long>(blockIdx.x) * NW + w; item < jobs.total_items; item += nwarps) {
+        while (j + 1 < jobs.n && jobs.job[j + 1].first_item <= item) ++j;
+        const BinJob &jb = jobs.job[j];
+        const double Mtot = jb.mom[0];
+        const float vb0 = static_cast<float>(jb.mom[2] / Mtot), vb1 = static_cast<float>(jb.mom[3] / Mtot),
+                    vb2 = static_cast<float>(jb.mom[4] / Mtot);
+        const int nh = jb.ng / 2 + 1;
+        const int64_t gstride = static_cast<int64_t>(jb.ng) * jb.ng * nh;
+        bin_item<float>(static_cast<const Cx<float> *>(jb.grids), gstride, jb.ng, jb.nbins, jb.thresh, jb.gf, jb.gh,
+                        vb0, vb1, vb2, jb.partials, static_cast<int>(item - jb.first_item), s_st[w]);
     }
 }
 
@@ -667,6 +739,51 @@ cudaError_t launch_bin_shells(const SpectraTables &t, const void *grids, const d
     return cudaGetLastError();
 }
 
+namespace {
+// k_finalize of shell sums `sums` ([kBinVals][nbins]) with the table's mode sums.
+cudaError_t finalize_sums(const SpectraTables &t, const pkmom_params &p, const double *moments_dev,
+                          const double *sums, double *out, cudaStream_t s, LaunchStats &st)
+{
+    FinalParams fp;
+    fp.V = p.box_L * p.box_L * p.box_L;
+    fp.kf = kTwoPi / p.box_L;
+    fp.ts = p.theta_scale;
+    fp.sub = p.subtract_shot_noise;
+    fp.bulk = p.bulk;
+    fp.iso = p.theta_sn_mode == 1;
+    fp.nbins = t.nbins;
+    k_finalize<<<(t.nbins + 127) / 128, 128, 0, s>>>(sums, t.mode_sums, moments_dev, fp, out);
+    st.launches++;
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_bin_batch(BinBatch &batch, const SpectraTables *const *tables, const pkmom_params *const *params,
+                             double *const *sums_of, double *const *out, int num_sms, cudaStream_t s,
+                             LaunchStats &st)
+{
+    long long first = 0;
+    for (int k = 0; k < batch.n; ++k) {
+        batch.job[k].first_item = first;
+        first += static_cast<long long>(batch.job[k].ng) * batch.job[k].nbins;
+    }
+    batch.total_items = first;
+    if (first == 0) return cudaSuccess;
+    const long long want = (first + kBinThreads / 32 - 1) / (kBinThreads / 32);
+    const unsigned blocks = static_cast<unsigned>(std::min<long long>(want, static_cast<long long>(num_sms) * 8));
+    k_bin_batch<<<blocks, kBinThreads, 0, s>>>(batch);
+    st.launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < batch.n; ++k) {
+        const BinJob &jb = batch.job[k];
+        k_reduce_items<kBinVals><<<jb.nbins, 256, 0, s>>>(jb.partials, jb.ng, jb.nbins, sums_of[k]);
+        st.launches++;
+        if ((e = finalize_sums(*tables[k], *params[k], jb.mom, sums_of[k], out[k], s, st)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_finalize(const SpectraTables &t, const pkmom_params &p, const double *moments_dev, double *out,
                             cudaStream_t s, LaunchStats &st, bool sums_ready)
 {
@@ -1009,6 +1126,7 @@ k_bin_mu(const Cx<T> *__restrict__ F, int64_t gstride, int ng, int nbins, int nm
                     const bool mir = l > 0 && mu_bin(-fn0, -fn1, -fl, e0, e1, e2, rn, nmu) == m;
                     if (!fwd && !mir) continue;
                     const int64_t mi = s_row[w][j] + l;
+                    if (!PK_IN(mi, gstride, kChkMode) || !PK_IN(l, nh, kChkMode)) continue;
                     const T g = s_g[w][j] * gh[l];
                     const T th = s_h[w][j] * static_cast<T>(hh[l]);
                     const Cx<T> dd = F[mi], p0 = F[gstride + mi], p1 = F[2 * gstride + mi], p2 = F[3 * gstride + mi];

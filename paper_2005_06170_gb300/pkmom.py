@@ -48,21 +48,30 @@ class Catalog(ctypes.Structure):
                 ("mass", ctypes.c_void_p), ("stride", ctypes.c_int64), ("dtype", ctypes.c_int)]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("cat", Catalog), ("p", Params), ("grids", ctypes.c_void_p), ("moments_dev", ctypes.c_void_p),
+                ("scratch", ctypes.c_void_p), ("scratch_bytes", ctypes.c_size_t), ("out_dev", ctypes.c_void_p),
+                ("deposit_tile", ctypes.c_int), ("list_cap", ctypes.c_int)]
+
+
+BATCH_MAX = 128
+
+
 class PkmomError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
         self.status = status
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    """Load libpkmom.so (building it in-tree with nvcc if it is missing or stale)."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    path = _build.build()
+def lib(checked: bool = False):
+    """Load libpkmom.so, or with checked=True libpkmom_checked.so (index tests before every
+    grid, buffer and bin access), building it in-tree with nvcc if missing or stale."""
+    if checked in _libs:
+        return _libs[checked]
+    path = _build.build(checked=checked)
     L = ctypes.CDLL(path)
     vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
     sig = {
@@ -91,12 +100,16 @@ def lib():
         "pkmom_estimate_host_async": (i32, [vp, ctypes.POINTER(Catalog), ctypes.POINTER(Params), vp, vp,
                                             ctypes.POINTER(ctypes.c_int64)]),
         "pkmom_wait": (i32, [vp, i64]),
+        "pkmom_batch_work_bytes": (ctypes.c_size_t, [i32, ctypes.POINTER(BatchItem)]),
+        "pkmom_estimate_batch": (i32, [vp, i32, ctypes.POINTER(BatchItem), vp, ctypes.c_size_t, vp]),
+        "pkmom_checked": (i32, []),
+        "pkmom_checked_selftest": (i32, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
         fn.restype = res
         fn.argtypes = args
-    _lib = L
+    _libs[checked] = L
     return L
 
 
@@ -105,7 +118,8 @@ EXPORTED = ("pkmom_params_default", "pkmom_create", "pkmom_destroy", "pkmom_stre
             "pkmom_fft", "pkmom_spectra", "pkmom_estimate", "pkmom_estimate_host", "pkmom_sync",
             "pkmom_timing_enable", "pkmom_timing_read", "pkmom_kernel_launches", "pkmom_spectra_static",
             "pkmom_set_tuning", "pkmom_assign_scratch_bytes_tuned", "pkmom_spectra_mu", "pkmom_context_bytes",
-            "pkmom_estimate_host_async", "pkmom_wait")
+            "pkmom_estimate_host_async", "pkmom_wait", "pkmom_batch_work_bytes", "pkmom_estimate_batch",
+            "pkmom_checked", "pkmom_checked_selftest")
 
 
 def params(box_L: float, ng: int, nbins: int, *, order: int = 4, precision: int = F32, kmin_kf: float = 1.0,
@@ -184,14 +198,17 @@ def catalog_from_numpy(pos: np.ndarray, vel: np.ndarray, mass: np.ndarray | None
 class Context:
     """A libpkmom context on one CUDA device (cuFFT plans and tables are cached in it)."""
 
-    def __init__(self, device: int = 0):
+    def __init__(self, device: int = 0, checked: bool = False):
+        """checked: use libpkmom_checked.so (index tests before every access)."""
+        self._L = lib(checked)
         self._h = ctypes.c_void_p()
-        self._check(lib().pkmom_create(ctypes.byref(self._h), int(device)))
+        self._check(self._L.pkmom_create(ctypes.byref(self._h), int(device)))
         self.device = device
+        self.checked = bool(checked)
 
     def close(self):
         if self._h:
-            lib().pkmom_destroy(self._h)
+            self._L.pkmom_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):
@@ -202,7 +219,7 @@ class Context:
 
     def _check(self, status):
         if status != 0:
-            L = lib()
+            L = self._L
             msg = L.pkmom_last_error(self._h).decode() if self._h else L.pkmom_strerror(status).decode()
             raise PkmomError(status, msg)
 
@@ -221,15 +238,15 @@ class Context:
 
     # -- the four calls of the C-ABI
     def assign(self, cat: Catalog, p: Params, grids, moments, scratch, stream=None):
-        self._check(lib().pkmom_assign(self._h, ctypes.byref(cat), ctypes.byref(p), grids.data_ptr(),
+        self._check(self._L.pkmom_assign(self._h, ctypes.byref(cat), ctypes.byref(p), grids.data_ptr(),
                                        moments.data_ptr(), scratch.data_ptr(), scratch.numel() * scratch.element_size(),
                                        _stream_ptr(stream)))
 
     def fft(self, p: Params, grids, stream=None):
-        self._check(lib().pkmom_fft(self._h, ctypes.byref(p), grids.data_ptr(), _stream_ptr(stream)))
+        self._check(self._L.pkmom_fft(self._h, ctypes.byref(p), grids.data_ptr(), _stream_ptr(stream)))
 
     def spectra(self, p: Params, grids, moments, out, stream=None):
-        self._check(lib().pkmom_spectra(self._h, ctypes.byref(p), grids.data_ptr(), moments.data_ptr(),
+        self._check(self._L.pkmom_spectra(self._h, ctypes.byref(p), grids.data_ptr(), moments.data_ptr(),
                                         out.data_ptr(), _stream_ptr(stream)))
 
     def spectra_mu(self, p: Params, grids, moments, nmu: int, direction=None, out=None, stream=None):
@@ -239,7 +256,7 @@ class Context:
         if out is None:
             out = torch.empty((MU_NROWS, p.nbins * nmu), dtype=torch.float64, device=grids.device)
         d = None if direction is None else (ctypes.c_double * 3)(*[float(x) for x in direction])
-        self._check(lib().pkmom_spectra_mu(self._h, ctypes.byref(p), grids.data_ptr(), moments.data_ptr(), d,
+        self._check(self._L.pkmom_spectra_mu(self._h, ctypes.byref(p), grids.data_ptr(), moments.data_ptr(), d,
                                            int(nmu), out.data_ptr(), _stream_ptr(stream)))
         return out
 
@@ -264,7 +281,7 @@ class Context:
         cat = catalog_from_tensors(pos, vel, mass)
         if out is None:
             out = torch.empty((NROWS, p.nbins), dtype=torch.float64, device=pos.device)
-        self._check(lib().pkmom_estimate(self._h, ctypes.byref(cat), ctypes.byref(p), out.data_ptr(),
+        self._check(self._L.pkmom_estimate(self._h, ctypes.byref(cat), ctypes.byref(p), out.data_ptr(),
                                          _stream_ptr(stream)))
         return out
 
@@ -273,7 +290,7 @@ class Context:
         cat = catalog_from_numpy(pos, vel, mass)
         if out is None:
             out = np.empty((NROWS, p.nbins), dtype=np.float64)
-        self._check(lib().pkmom_estimate_host(self._h, ctypes.byref(cat), ctypes.byref(p), out.ctypes.data,
+        self._check(self._L.pkmom_estimate_host(self._h, ctypes.byref(cat), ctypes.byref(p), out.ctypes.data,
                                               _stream_ptr(stream)))
         return out
 
@@ -287,40 +304,70 @@ class Context:
         if out.dtype != np.float64 or not out.flags["C_CONTIGUOUS"] or out.size < NROWS * p.nbins:
             raise ValueError("out must be a C-contiguous float64 array of NROWS * nbins values")
         t = ctypes.c_int64()
-        self._check(lib().pkmom_estimate_host_async(self._h, ctypes.byref(cat), ctypes.byref(p), out.ctypes.data,
+        self._check(self._L.pkmom_estimate_host_async(self._h, ctypes.byref(cat), ctypes.byref(p), out.ctypes.data,
                                                     _stream_ptr(stream), ctypes.byref(t)))
         return int(t.value)
 
     def wait(self, ticket: int):
         """pkmom_wait: blocks until the result of that ticket is on the host."""
-        self._check(lib().pkmom_wait(self._h, int(ticket)))
+        self._check(self._L.pkmom_wait(self._h, int(ticket)))
+
+    def estimate_batch(self, items, work, stream=None):
+        """pkmom_estimate_batch over a ctypes array of BatchItem (see batch_items) with a
+        device work buffer of at least batch_work_bytes(items) bytes."""
+        self._check(self._L.pkmom_estimate_batch(self._h, len(items), items, work.data_ptr(),
+                                               work.numel() * work.element_size(), _stream_ptr(stream)))
 
     def sync(self, stream=None):
-        self._check(lib().pkmom_sync(self._h, _stream_ptr(stream)))
+        self._check(self._L.pkmom_sync(self._h, _stream_ptr(stream)))
 
     # -- instrumentation
     def timing(self, on: bool):
-        self._check(lib().pkmom_timing_enable(self._h, int(bool(on))))
+        self._check(self._L.pkmom_timing_enable(self._h, int(bool(on))))
 
     def timing_read(self) -> dict:
         ms = (ctypes.c_double * len(STAGES))()
         calls = (ctypes.c_int64 * len(STAGES))()
-        self._check(lib().pkmom_timing_read(self._h, ms, calls))
+        self._check(self._L.pkmom_timing_read(self._h, ms, calls))
         return {s: (ms[i], calls[i]) for i, s in enumerate(STAGES)}
 
+    def checked_selftest(self, stream=None):
+        """pkmom_checked_selftest (checked build): the next sync raises PKMOM_EDATA."""
+        self._check(self._L.pkmom_checked_selftest(self._h, _stream_ptr(stream)))
+
     def kernel_launches(self) -> int:
-        return int(lib().pkmom_kernel_launches(self._h))
+        return int(self._L.pkmom_kernel_launches(self._h))
 
     def set_tuning(self, deposit_tile: int = -1, list_cap: int = -1):
         """Deposit tile shape and particle-list capacity (-1: automatic); see include/pkmom.h."""
-        self._check(lib().pkmom_set_tuning(self._h, int(deposit_tile), int(list_cap)))
+        self._check(self._L.pkmom_set_tuning(self._h, int(deposit_tile), int(list_cap)))
 
     def scratch_bytes_tuned(self, p: Params, n: int) -> int:
-        return int(lib().pkmom_assign_scratch_bytes_tuned(self._h, ctypes.byref(p), n))
+        return int(self._L.pkmom_assign_scratch_bytes_tuned(self._h, ctypes.byref(p), n))
 
     def context_bytes(self) -> int:
         """Device bytes the context holds (cuFFT plan workspaces, tables, owned buffers)."""
-        return int(lib().pkmom_context_bytes(self._h))
+        return int(self._L.pkmom_context_bytes(self._h))
+
+
+def batch_items(entries):
+    """entries: (catalog, params, grids, moments, scratch, out, deposit_tile, list_cap) per
+    catalogue (Catalog, Params and device tensors) -> a ctypes array of BatchItem."""
+    arr = (BatchItem * len(entries))()
+    for it, (cat, p, grids, mom, scratch, out, tile, cap) in zip(arr, entries):
+        it.cat, it.p = cat, p
+        it.grids, it.moments_dev, it.scratch = grids.data_ptr(), mom.data_ptr(), scratch.data_ptr()
+        it.scratch_bytes = scratch.numel() * scratch.element_size()
+        it.out_dev = out.data_ptr()
+        it.deposit_tile, it.list_cap = int(tile), int(cap)
+    return arr
+
+
+def batch_work_bytes(items) -> int:
+    n = int(lib().pkmom_batch_work_bytes(len(items), items))
+    if n == 0:
+        raise PkmomError(-1, "invalid batch items")
+    return n
 
 
 def spectra_static(p: Params, grids, moments, out, stream=None):
@@ -344,5 +391,5 @@ def as_dict(out) -> dict:
     return {k: a[i] for k, i in ROW.items()}
 
 
-def library_path() -> str:
-    return os.path.abspath(_build.LIB)
+def library_path(checked: bool = False) -> str:
+    return os.path.abspath(_build.LIB_CHECKED if checked else _build.LIB)

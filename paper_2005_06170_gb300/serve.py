@@ -111,6 +111,8 @@ class Server:
         gives every lane the default priority. strict_lanes: large requests run only on
         the large lanes (one at a time per lane, in arrival order) and small ones only on
         the others; otherwise either kind takes any free lane when its own are busy.
+        "high" gives the large lanes the greatest priority instead, so that a large request
+        runs at nearly its own speed and small ones fill the gaps.
 
         Measured on a Poisson stream (20 requests/s, 1e5 to 1.3e8 particles, grids 128^3
         to 1024^3) against one request at a time: with four lanes, one of them strict for
@@ -124,18 +126,23 @@ class Server:
         self.device = device
         self.ctxs = [pkmom.Context(device) for _ in range(lanes)]
         lo, hi = torch.cuda.Stream.priority_range()  # (least, greatest) priority
-        if large_priority not in ("low", "same"):
-            raise ValueError("large_priority must be 'low' or 'same'")
+        if large_priority not in ("low", "same", "high"):
+            raise ValueError("large_priority must be 'low', 'same' or 'high'")
         if large_lanes is None:
             large_lanes = 1 if lanes > 1 else 0
         if not 0 <= large_lanes < lanes:
             raise ValueError("large_lanes must leave at least one lane for small requests")
         self.n_small = lanes - large_lanes
         self.large_bytes = large_bytes
-        split = large_priority == "low" and large_lanes > 0
         self.strict = bool(strict_lanes) and large_lanes > 0
-        self.streams = [torch.cuda.Stream(device=device, priority=(hi if k < self.n_small else lo) if split else 0)
-                        for k in range(lanes)]
+
+        def prio(k):  # stream priority of lane k
+            if large_lanes == 0 or large_priority == "same":
+                return 0
+            small = k < self.n_small
+            return (hi if small else lo) if large_priority == "low" else (lo if small else hi)
+
+        self.streams = [torch.cuda.Stream(device=device, priority=prio(k)) for k in range(lanes)]
         self.lane_free = [True] * lanes
         # device memory each lane's context keeps between requests (cuFFT plans and
         # per-grid tables), charged to the budget beside the running requests

@@ -66,3 +66,11 @@ def test_create_without_device_fails_cleanly():
     h = ctypes.c_void_p()
     assert pkmom.lib().pkmom_create(ctypes.byref(h), 0) != 0
     assert not h.value
+
+
+def test_checked_library_exports_the_same_symbols():
+    Lc = pkmom.lib(checked=True)
+    for name in declared_symbols():
+        assert hasattr(Lc, name), name
+    assert Lc.pkmom_checked() == 1
+    assert pkmom.lib().pkmom_checked() == 0

@@ -127,3 +127,26 @@ def test_requests_compare_by_identity():
     assert a != b and a == a
     q = [a, b]
     assert q.index(b) == 1
+
+
+def test_autotuner_restricted_tiles(tmp_path):
+    """A restricted choice times only the allowed tiles and is cached under its own key."""
+    calls = []
+
+    def timer(ctx, cat, p, tile, cap):
+        calls.append((tile, cap))
+        return {0: 3.0, 2: 1.0, 7: 2.0}.get(tile, 5.0)
+
+    class P:
+        ng, precision = 64, 0
+
+    class C:
+        n = 64 ** 3
+
+    t = autotune.Autotuner(path=str(tmp_path / "t.json"), timer=timer)
+    assert t.choose(None, C, P, "g") == (2, -1)
+    free = len(calls)
+    assert t.choose(None, C, P, "g", tiles=(0, 7))[0] == 7
+    assert all(tile in (0, 7) for tile, _ in calls[free:])
+    assert t.choose(None, C, P, "g", tiles=(0, 7))[0] == 7  # cached
+    assert len(calls) == free + len([c for c in autotune.candidates(64, 0) if c[0] in (0, 7)])

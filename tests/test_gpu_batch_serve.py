@@ -38,7 +38,8 @@ def _single(pk, ctx, d, p):
     return out.cpu().numpy()
 
 
-def test_batch_graph_equals_single_runs(gpu_lib):
+@pytest.mark.parametrize("fused", [True, False])
+def test_batch_graph_equals_single_runs(gpu_lib, fused):
     import torch
 
     from paper_2005_06170_gb300.batch import BatchRunner
@@ -48,7 +49,7 @@ def test_batch_graph_equals_single_runs(gpu_lib):
     params = [pk.params(L, ng, 12, theta_scale=0.02) for _, L, ng in items]
     ctx = pk.Context(0)
     ref = [_single(pk, ctx, d, p) for d, p in zip(devs, params)]
-    runner = BatchRunner(devs, params, lanes=3, use_graph=True)
+    runner = BatchRunner(devs, params, lanes=3, use_graph=True, fused=fused)
     first = [o.cpu().numpy() for o in runner.run()]  # eager run, then capture
     torch.cuda.synchronize()
     for o in runner.run():  # graph replay
@@ -194,3 +195,52 @@ def test_served_catalogue_written_on_the_callers_stream(gpu_lib):
     got = fut.result(timeout=120)
     srv.close()
     np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.nanmax(np.abs(ref)), equal_nan=True)
+
+
+def test_estimate_batch_through_the_c_abi(gpu_lib):
+    """pkmom_estimate_batch on catalogues that take every deposit path (16^3 gather tiles
+    in the persistent kernel, home tiles, another order, FP64, the direct BL stencil, an
+    8^3 tile by tuning) equals pkmom_estimate on each, in the same context (bit for bit:
+    the same kernels per tile and per binning item, reductions in the same order)."""
+    import torch
+    pk = gpu_lib
+    specs = [  # (kind, size, L, ng, precision, order, bl_radius, tile)
+        ("p", 3000, 80.0, 32, pk.F32, 4, 0, -1), ("z", 32, 200.0, 32, pk.F32, 4, 0, -1),
+        ("p", 40000, 150.0, 64, pk.F32, 4, 0, 0), ("p", 5000, 100.0, 48, pk.F32, 2, 0, -1),
+        ("p", 4000, 90.0, 32, pk.F64, 4, 0, -1), ("z", 16, 100.0, 32, pk.F32, 4, 3, -1),
+        ("p", 20000, 120.0, 64, pk.F32, 4, 0, 3), ("z", 24, 300.0, 48, pk.F32, 4, 0, -1)]
+    ctx = pk.Context(0)
+    entries, refs = [], []
+    keep = []
+    for i, (kind, size, L, ng, prec, order, blr, tile) in enumerate(specs):
+        dt = np.float32 if prec == pk.F32 else np.float64
+        c = (catalogs.poisson(size, L, seed=800 + i, dtype=dt) if kind == "p"
+             else catalogs.zeldovich(size, L, seed=900 + i, dtype=dt))
+        pos, vel = torch.from_numpy(c["pos"]).cuda(), torch.from_numpy(c["vel"]).cuda()
+        p = pk.params(L, ng, 10, precision=prec, order=order, bl_radius=blr, theta_scale=0.01)
+        ctx.set_tuning(tile, -1)
+        ref = ctx.estimate(pos, vel, p)
+        ctx.sync()
+        ctx.set_tuning(-1, -1)
+        refs.append(ref.cpu().numpy())
+        tdt = torch.float32 if prec == pk.F32 else torch.float64
+        grids = torch.empty(pk.Context.grid_bytes(ng, prec) // (4 if prec == pk.F32 else 8), dtype=tdt,
+                            device="cuda")
+        mom = torch.zeros(16, dtype=torch.float64, device="cuda")
+        cat = pk.catalog_from_tensors(pos, vel)
+        ctx.set_tuning(tile, -1)
+        scratch = torch.empty(ctx.scratch_bytes_tuned(p, cat.n), dtype=torch.uint8, device="cuda")
+        ctx.set_tuning(-1, -1)
+        out = torch.full((pk.NROWS, 10), -1.0, dtype=torch.float64, device="cuda")
+        entries.append((cat, p, grids, mom, scratch, out, tile, -1))
+        keep.append((pos, vel))
+    arr = pk.batch_items(entries)
+    work = torch.empty(pk.batch_work_bytes(arr), dtype=torch.uint8, device="cuda")
+    l0 = ctx.kernel_launches()
+    ctx.estimate_batch(arr, work)
+    ctx.sync()
+    assert ctx.kernel_launches() > l0
+    for e, ref in zip(entries, refs):
+        got = e[5].cpu().numpy()
+        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.nanmax(np.abs(ref)), equal_nan=True)
+    ctx.close()

@@ -382,3 +382,22 @@ def test_config2_full_size_both_bulk_variants(ctx, gpu_lib):
     o = run_oracle(cat, L, 256, 128)
     worst = compare(g, o, 1e-4)
     print(f"config 2 worst normalised shell error {worst:.3e}")
+
+
+def test_misaligned_grids_are_rejected(ctx, gpu_lib):
+    """The deposit writes grid rows in 8-byte pairs: grids and scratch must be 16-byte
+    aligned, and a pointer that is not gives PKMOM_EINVAL (nothing is launched)."""
+    import torch
+    pk = gpu_lib
+    p = pk.params(100.0, 16, 4)
+    pos = torch.rand((100, 3), device="cuda") * 100.0
+    vel = torch.zeros_like(pos)
+    cat = pk.catalog_from_tensors(pos, vel)
+    grids = torch.empty(pk.Context.grid_bytes(16) // 4 + 4, dtype=torch.float32, device="cuda")
+    mom = torch.zeros(16, dtype=torch.float64, device="cuda")
+    scratch = torch.empty(pk.Context.scratch_bytes(p, 100), dtype=torch.uint8, device="cuda")
+    with pytest.raises(pk.PkmomError) as e:
+        ctx.assign(cat, p, grids[1:], mom, scratch)
+    assert e.value.status == -1
+    ctx.assign(cat, p, grids[4:], mom, scratch)  # 16 bytes in: fine
+    ctx.sync()
