@@ -54,6 +54,7 @@ struct pkmom_ctx {
     void *aslot[2] = {nullptr, nullptr};
     size_t aslot_bytes[2] = {0, 0};
     cudaStream_t copy_stream = nullptr;
+    cudaStream_t aux_stream = nullptr;  // reads of the error word
     cudaEvent_t slot_copied[2] = {nullptr, nullptr};
     cudaEvent_t slot_free[2] = {nullptr, nullptr};
     cudaEvent_t done[kRing] = {};
@@ -377,10 +378,16 @@ pkmom_status stage_catalog(pkmom_ctx *ctx, const pkmom_catalog &cat, size_t elem
 // checked builds a failed index test of any kernel on this device.
 pkmom_status check_error_word(pkmom_ctx *ctx)
 {
+    // read on a stream of the context's own, so that the read waits for nothing but itself
+    // (a copy on the legacy default stream would wait for every blocking stream's work)
+    if (!ctx->aux_stream) PK_CUDA(cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking), "aux stream");
     int flag = 0;
-    PK_CUDA(cudaMemcpy(&flag, ctx->d_err, sizeof flag, cudaMemcpyDeviceToHost), "read error word");
+    PK_CUDA(cudaMemcpyAsync(&flag, ctx->d_err, sizeof flag, cudaMemcpyDeviceToHost, ctx->aux_stream),
+            "read error word");
+    PK_CUDA(cudaStreamSynchronize(ctx->aux_stream), "read error word");
     if (flag) {
-        PK_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)), "clear error word");
+        PK_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->aux_stream), "clear error word");
+        PK_CUDA(cudaStreamSynchronize(ctx->aux_stream), "clear error word");
         return fail(ctx, PKMOM_EDATA, "catalogue held non-finite or out-of-range positions (|x ng/L| >= 2^30)");
     }
     if (PKMOM_CHECKED) {
@@ -475,6 +482,7 @@ pkmom_status pkmom_destroy(pkmom_ctx *ctx)
     for (auto e : ctx->done)
         if (e) cudaEventDestroy(e);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
     cudaFree(ctx->mu_partials);
     cudaFree(ctx->mu_sums);
     cudaFree(ctx->d_err);
