@@ -368,34 +368,29 @@ k_moments(const T *__restrict__ vx, const T *__restrict__ vy, const T *__restric
 
 // FP32 interleaved (n, 3) velocities, 16-byte aligned: four particles per thread read
 // as three 128-bit loads ((v0x v0y v0z v1x) (v1y v1z v2x v2y) (v2z v3x v3y v3z)), and
-// four masses as one. The same sums as k_moments; the n % 4 last particles are added
-// by the first lanes of block 0.
+// four masses as one. The same sums as k_moments, kept by each lane in compensated
+// (Kahan) FP32 pairs over all of its particles, so that no warp reduction waits inside
+// the loop; each lane's pairs go to FP64 once at the end and are summed in a fixed
+// order. The n % 4 last particles are added by the first lanes of block 0.
 __global__ void __launch_bounds__(256)
 k_moments_v3(const float *__restrict__ v, const float *__restrict__ mass, int64_t n,
              double *__restrict__ partials, unsigned *__restrict__ qmax_bits)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __shared__ double s_part[256 / 32][kMomentVals];
-    if (lane < kMomentVals) s_part[warp][lane] = 0.0;
-    __syncwarp();
     float qmax[4] = {0.f, 0.f, 0.f, 0.f};
-    float grp[kMomentVals];
+    float sum[kMomentVals], cmp[kMomentVals];  // the sum of a value is sum - cmp
 #pragma unroll
-    for (int k = 0; k < kMomentVals; ++k) grp[k] = 0.f;
-    int gcount = 0;
+    for (int k = 0; k < kMomentVals; ++k) sum[k] = 0.f, cmp[k] = 0.f;
     const int64_t nq = n / 4;
     const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x;
     const float4 *v4 = reinterpret_cast<const float4 *>(v);
     const float4 *m4 = reinterpret_cast<const float4 *>(mass);
-    auto flush = [&]() {
-#pragma unroll
-        for (int k = 0; k < kMomentVals; ++k) {
-            float x = grp[k];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            if (lane == 0) s_part[warp][k] += static_cast<double>(x);
-            grp[k] = 0.f;
-        }
+    auto kahan = [&](int k, float x) {
+        const float y = __fsub_rn(x, cmp[k]);
+        const float t = __fadd_rn(sum[k], y);
+        cmp[k] = __fsub_rn(__fsub_rn(t, sum[k]), y);
+        sum[k] = t;
     };
     auto add = [&](float m, float v0, float v1, float v2) {
         const float m2 = m * m;
@@ -403,42 +398,40 @@ k_moments_v3(const float *__restrict__ v, const float *__restrict__ mass, int64_
         qmax[1] = fmaxf(qmax[1], fabsf(m * v0));
         qmax[2] = fmaxf(qmax[2], fabsf(m * v1));
         qmax[3] = fmaxf(qmax[3], fabsf(m * v2));
-        grp[0] += m;
-        grp[1] += m2;
-        grp[2] += m * v0;
-        grp[3] += m * v1;
-        grp[4] += m * v2;
-        grp[5] += m2 * v0;
-        grp[6] += m2 * v1;
-        grp[7] += m2 * v2;
-        grp[8] += m2 * v0 * v0;
-        grp[9] += m2 * v1 * v1;
-        grp[10] += m2 * v2 * v2;
-        grp[11] += m2 * v0 * v1;
-        grp[12] += m2 * v0 * v2;
-        grp[13] += m2 * v1 * v2;
+        kahan(0, m);
+        kahan(1, m2);
+        kahan(2, m * v0);
+        kahan(3, m * v1);
+        kahan(4, m * v2);
+        kahan(5, m2 * v0);
+        kahan(6, m2 * v1);
+        kahan(7, m2 * v2);
+        kahan(8, m2 * v0 * v0);
+        kahan(9, m2 * v1 * v1);
+        kahan(10, m2 * v2 * v2);
+        kahan(11, m2 * v0 * v1);
+        kahan(12, m2 * v0 * v2);
+        kahan(13, m2 * v1 * v2);
     };
-    for (int64_t wb = static_cast<int64_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); wb < nq; wb += step) {
-        const int64_t q = wb + lane;
-        if (q < nq) {
-            const float4 a = v4[3 * q], b = v4[3 * q + 1], c = v4[3 * q + 2];
-            const float4 mm = mass ? m4[q] : make_float4(1.f, 1.f, 1.f, 1.f);
-            add(mm.x, a.x, a.y, a.z);
-            add(mm.y, a.w, b.x, b.y);
-            add(mm.z, b.z, b.w, c.x);
-            add(mm.w, c.y, c.z, c.w);
-        }
-        gcount += 4;
-        if (gcount >= kGroup) {
-            flush();
-            gcount = 0;
-        }
+    for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < nq; q += step) {
+        const float4 a = v4[3 * q], b = v4[3 * q + 1], c = v4[3 * q + 2];
+        const float4 mm = mass ? m4[q] : make_float4(1.f, 1.f, 1.f, 1.f);
+        add(mm.x, a.x, a.y, a.z);
+        add(mm.y, a.w, b.x, b.y);
+        add(mm.z, b.z, b.w, c.x);
+        add(mm.w, c.y, c.z, c.w);
     }
     if (blockIdx.x == 0 && warp == 0) {
         const int64_t i = 4 * nq + lane;
         if (i < n) add(mass ? mass[i] : 1.f, v[3 * i], v[3 * i + 1], v[3 * i + 2]);
     }
-    flush();
+#pragma unroll
+    for (int k = 0; k < kMomentVals; ++k) {
+        double x = static_cast<double>(sum[k]) - static_cast<double>(cmp[k]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) s_part[warp][k] = x;
+    }
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const unsigned bits = __reduce_max_sync(0xffffffffu, __float_as_uint(qmax[f]));
@@ -446,9 +439,9 @@ k_moments_v3(const float *__restrict__ v, const float *__restrict__ mass, int64_
     }
     __syncthreads();
     if (threadIdx.x < kMomentVals) {
-        double sum = 0.0;
-        for (int w = 0; w < 256 / 32; ++w) sum += s_part[w][threadIdx.x];
-        partials[static_cast<int64_t>(blockIdx.x) * kMomentWords + threadIdx.x] = sum;
+        double total = 0.0;
+        for (int w = 0; w < 256 / 32; ++w) total += s_part[w][threadIdx.x];
+        partials[static_cast<int64_t>(blockIdx.x) * kMomentWords + threadIdx.x] = total;
     }
 }
 
