@@ -1687,6 +1687,13 @@ k_deposit_home(const Record<float> *__restrict__ rec, const uint32_t *__restrict
 #pragma unroll
         for (int z = 0; z <= kHomeT; ++z) o[z] = offsets[key + z];
         const uint32_t b = o[0], cnt = o[kHomeT] - b;
+        // the column's records are read later, cell by cell: ask L2 for them now (128-byte
+        // lines covering the column's contiguous range, at most 32 lines per column)
+        {
+            const char *r0 = reinterpret_cast<const char *>(rec + b);
+            const uint32_t lines = cnt ? min((cnt * 32u + 127u) / 128u + 1u, 32u) : 0u;
+            for (uint32_t l = 0; l < lines; ++l) asm volatile("prefetch.L2 [%0];" ::"l"(r0 + 128 * l));
+        }
         // a node receives from 4 consecutive cells of a column: the largest such count
         uint32_t win = 0;
 #pragma unroll
