@@ -764,9 +764,9 @@ k_deposit(const Record<T> *__restrict__ rec, const uint32_t *__restrict__ offset
         const int l2 = k % T2, l01 = k / T2;
         const int l1 = l01 % T1, l0 = l01 / T1;
         const int64_t gi = (static_cast<int64_t>(t0 + l0) * ng + (t1 + l1)) * (ng + 2) + t2 + l2;
+        if (!PK_IN(gi, grid_elems, kChkGrid)) continue;
 #pragma unroll
-        if (PK_IN(gi, grid_elems, kChkGrid))
-            for (int f = 0; f < 4; ++f) grids[f * grid_elems + gi] = acc[f * C::TN + k];
+        for (int f = 0; f < 4; ++f) grids[f * grid_elems + gi] = acc[f * C::TN + k];
     }
 }
 
