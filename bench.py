@@ -317,16 +317,43 @@ def roofline(workload, stage_ms, n, ng, prec, bl_radius, unit_mass=True):
             "issue": issue, "avg_launch_ms": ms}
 
 
+def _isqrt(x):
+    r = np.floor(np.sqrt(x.astype(np.float64))).astype(np.int64)
+    r -= (r * r > x)
+    r += ((r + 1) * (r + 1) <= x)
+    return r
+
+
+def in_shell_modes(ng, umin=1.0, umax=None):
+    """Modes (n0, n1, l) of the ng^3 half spectrum with umin <= |n| <= umax (umax: ng/2),
+    the ones the binning reads: the shells of the bench's workloads span that range."""
+    umax = ng / 2 if umax is None else umax
+    lo2, hi2 = int(np.ceil(umin * umin)), int(np.floor(umax * umax))
+    n = np.arange(-(ng // 2), ng // 2, dtype=np.int64)
+    r2 = n[:, None] ** 2 + n[None, :] ** 2
+    top = hi2 - r2
+    lmax = np.minimum(_isqrt(np.maximum(top, 0)), ng // 2)
+    need = lo2 - r2
+    lmin = np.where(need <= 0, 0, _isqrt(np.maximum(need - 1, 0)) + 1)
+    cnt = np.where(top >= 0, np.maximum(lmax - lmin + 1, 0), 0)
+    return int(cnt.sum())
+
+
 def bin_roofline(stage_ms, ng, prec):
-    """The binning stage against HBM: 16 B per half-spectrum cell read (four complex FP32
-    values), the whole ng x ng x (ng/2 + 1) half spectra."""
+    """The binning stage against HBM. `achieved` counts the bytes the binning must read:
+    the four complex values (32 B in FP32) of every half-spectrum mode inside the shell
+    range (about pi/6 of the half spectrum when the shells end at the Nyquist frequency);
+    `frac_16B_per_cell` counts the whole ng x ng x (ng/2 + 1) half spectra (16 B per grid
+    cell), which the kernel does not read in full."""
     peak, _ = load_peaks()
     elem = 4 if prec == "f32" else 8
-    b = 4 * 2 * elem * ng * ng * (ng // 2 + 1)
+    full = 4 * 2 * elem * ng * ng * (ng // 2 + 1)
+    b = 4 * 2 * elem * in_shell_modes(ng)
     ms = stage_ms["bin"]
     gbs = b / (ms * 1e-3) / 1e9 if ms > 0 else None
     return {"kernel": "k_bin_shells + k_reduce_items", "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
-            "frac": gbs / peak if gbs else None, "algorithmic_bytes_per_launch": b, "avg_launch_ms": ms}
+            "frac": gbs / peak if gbs else None, "algorithmic_bytes_per_launch": b, "avg_launch_ms": ms,
+            "bytes_16B_per_cell": full, "frac_16B_per_cell": full / (ms * 1e-3) / 1e9 / peak if ms > 0 else None}
 
 
 def e2e_host(ctx, cat, p, stream, torch, k_pipe=20, k_single=5):

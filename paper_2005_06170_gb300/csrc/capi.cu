@@ -857,6 +857,7 @@ pkmom_status pkmom_estimate_batch(pkmom_ctx *ctx, int n, const pkmom_batch_item 
     {
         StageTimer t(ctx, PKMOM_STAGE_BIN, st);
         BinBatch bb{};
+        bb.counter = reinterpret_cast<unsigned *>(counter);  // the deposit's counter, free again
         std::vector<const SpectraTables *> btabs;
         std::vector<const pkmom_params *> bpar;
         std::vector<double *> bsums, bout;

@@ -102,13 +102,15 @@ struct BinJob {
     const int *thresh;
     const float *gf, *gh;
     double *partials;
-    long long first_item;
-    int ng, nbins;
+    const uint32_t *order;  // the catalogue's non-empty items (SpectraTables::bin_order)
+    long long first_item;   // of this catalogue in the batch's list of non-empty items
+    int ng, nbins, nwork;
 };
 struct BinBatch {
     BinJob job[kBatchMax];
     int n;
     long long total_items;
+    unsigned *counter;  // next item of the batch; zeroed before the launch
 };
 
 // ---------------------------------------------------------------- assign.cu
@@ -154,6 +156,11 @@ struct SpectraTables {
     int bin_blocks = 0;
     double *item_partials = nullptr;  // [ng * nbins][kBinVals] (shell-major binning)
     int shell_blocks = 0;
+    // the (slab, shell) items that hold modes, i0 * nbins + b, slabs by increasing |n0|
+    // (the larger items first); items missing from it are empty and never written
+    uint32_t *bin_order = nullptr;
+    int bin_nwork = 0;
+    unsigned *bin_counter = nullptr;  // [2]: next entry of bin_order, blocks done (zero between launches)
     size_t bytes = 0;            // device bytes of all the arrays above
 };
 cudaError_t build_spectra_tables(SpectraTables &t, int ng, int order, bool direct, int nbins, double umin,
@@ -163,9 +170,10 @@ cudaError_t launch_bin(const SpectraTables &t, const void *grids, const double *
                        LaunchStats &st);
 cudaError_t launch_bin_shells(const SpectraTables &t, const void *grids, const double *moments_dev, cudaStream_t s,
                               LaunchStats &st);
-// Persistent binning over the (slab, shell) items of many FP32 catalogues, each into its
-// own partials (ng * nbins * kBinVals doubles), then per catalogue the fixed-order
-// reduction into sums[kBinVals * nbins] (sums_of[k]) and the finalisation into out[k].
+// Persistent binning over the non-empty (slab, shell) items of many FP32 catalogues, each
+// into its own partials (ng * nbins * kBinVals doubles), then per catalogue the
+// fixed-order reduction into sums[kBinVals * nbins] (sums_of[k]) and the finalisation
+// into out[k]. batch.counter: 4 bytes of device memory the call zeroes and uses.
 cudaError_t launch_bin_batch(BinBatch &batch, const SpectraTables *const *tables, const pkmom_params *const *params,
                              double *const *sums_of, double *const *out, int num_sms, cudaStream_t s,
                              LaunchStats &st);

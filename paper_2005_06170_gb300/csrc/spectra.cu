@@ -193,6 +193,50 @@ __device__ __forceinline__ double warp_sum_pair(double hi, double lo)
     return v;
 }
 
+// (hi, lo) += (bh, bl) for unevaluated float pairs: a two-sum of the high parts, then
+// the low parts and the rounding error added and renormalised.
+__device__ __forceinline__ void pair_add(float &hi, float &lo, float bh, float bl)
+{
+    const float sh = __fadd_rn(hi, bh);
+    const float bb = __fsub_rn(sh, hi);
+    const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(sh, bb)), __fsub_rn(bh, bb));
+    const float t = __fadd_rn(se, __fadd_rn(lo, bl));
+    hi = __fadd_rn(sh, t);
+    lo = __fsub_rn(t, __fsub_rn(hi, sh));
+}
+__device__ __forceinline__ void pair_add(double &hi, double &lo, double bh, double bl) { hi += bh + bl, lo = 0.0; }
+
+// Warp sums of 8 values per lane (value k as the pair hi[k] + lo[k]) by reduce-scatter:
+// at the steps across lanes 16, 8 and 4 apart each lane keeps half of the values it
+// still holds and adds its partner's copy of them, then the lanes 2 and 1 apart add their
+// single values. Lane L ends with the sum of value ((L >> 2) & 7) over the warp, the
+// same in lanes 4k..4k+3; 9 pair additions per lane instead of 40 for eight butterflies.
+// Returned as FP64; fixed order.
+template <typename T>
+__device__ __forceinline__ double warp_scatter_sum8(T (&hi)[8], T (&lo)[8])
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int half = 4, o = 16; half >= 1; half >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;  // keeps the upper half of its values
+#pragma unroll
+        for (int j = 0; j < half; ++j) {
+            const T mh = up ? hi[j + half] : hi[j], ml = up ? lo[j + half] : lo[j];
+            const T sh = up ? hi[j] : hi[j + half], sl = up ? lo[j] : lo[j + half];
+            const T rh = __shfl_xor_sync(full, sh, o), rl = __shfl_xor_sync(full, sl, o);
+            hi[j] = mh, lo[j] = ml;
+            pair_add(hi[j], lo[j], rh, rl);
+        }
+    }
+#pragma unroll
+    for (int o = 2; o >= 1; o >>= 1) {
+        const T rh = __shfl_xor_sync(full, hi[0], o), rl = __shfl_xor_sync(full, lo[0], o);
+        pair_add(hi[0], lo[0], rh, rl);
+    }
+    return static_cast<double>(hi[0]) + static_cast<double>(lo[0]);
+}
+
 // floor(sqrt(x)) for 0 <= x < 2^24, exact
 __device__ __forceinline__ int isqrt_floor(int x)
 {
@@ -204,21 +248,21 @@ __device__ __forceinline__ int isqrt_floor(int x)
 
 // Shell-major binning. Work item (n0, b): all modes of shell b in the slab n_x = n0,
 // one warp per item, so each lane keeps one set of sums for the whole item. Items are
-// ordered slab-major, so the items running together read the same slab (which stays
-// in L2). The shell is the integer interval thresh[b] <= |n|^2 < thresh[b + 1]; in each
+// taken slab by slab, so the items running together read the same few slabs (which
+// stay in L2); items that hold no mode are not run. The shell is the integer interval thresh[b] <= |n|^2 < thresh[b + 1]; in each
 // row (n0, n1) its modes form one run of l, found with exact integer square roots (no
 // mode is tested against a table). The runs of 32 rows are laid end to end and the
 // warp walks the joined list 32 modes at a time (lane j takes the j-th mode), so all
 // lanes work and consecutive lanes read consecutive modes of a row. The seven per-mode
 // values are summed with Kahan-compensated adds in the grid precision; one warp
-// reduction per item (float pairs for FP32) writes partials[item][kBinVals] in FP64, and
-// k_reduce_items adds the items of each shell in a fixed order.
-// Per-warp staging of the rows of one item (k_bin_shells, k_bin_batch).
-template <typename T>
+// reduce-scatter per item (float pairs for FP32) writes partials[item][kBinVals] in FP64,
+// and k_reduce_items adds the items of each shell in a fixed order.
+// Per-warp staging of the rows of one item (k_bin_shells, k_bin_batch): the non-empty
+// rows of a group of 32, in order, each as (first mode's index in the joined list, first
+// l, n1, then for FP32 the bits of the row's factor g0 * gf[i1], for FP64 i1), one
+// 16-byte load.
 struct BinWarpStage {
-    int lo[32], pre[32], n1[32];
-    int64_t row[32];
-    T g[32];
+    int4 rows[32];
 };
 
 // One item (n0 = slab i0, shell b) of the shell-major binning, by one warp: writes
@@ -227,7 +271,7 @@ template <typename T>
 __device__ __forceinline__ void bin_item(const Cx<T> *__restrict__ F, int64_t gstride, int ng, int nbins,
                                          const int *__restrict__ thresh, const T *__restrict__ gf,
                                          const T *__restrict__ gh, T vb0, T vb1, T vb2, double *__restrict__ partials,
-                                         int item, BinWarpStage<T> &st)
+                                         int item, BinWarpStage &st)
 {
     const int nh = ng / 2 + 1;
     const int lane = threadIdx.x & 31;
@@ -240,7 +284,11 @@ __device__ __forceinline__ void bin_item(const Cx<T> *__restrict__ F, int64_t gs
 #pragma unroll
     for (int k = 0; k < kBinVals; ++k) s[k] = T(0), c[k] = T(0);
     const int rem = hi2 - 1 - n0 * n0;
-    if (hi2 > lo2 && rem >= 0) {
+    if (hi2 <= lo2 || rem < 0) {  // the shell misses this slab: zero sums, no reduction
+        if (lane < kBinVals) partials[static_cast<int64_t>(item) * kBinVals + lane] = 0.0;
+        return;
+    }
+    {
         const int R1 = isqrt_floor(rem);
         const int n1lo = max(-ng / 2, -R1), n1hi = min(ng / 2 - 1, R1);
         const T g0 = gf[i0];
@@ -266,26 +314,37 @@ __device__ __forceinline__ void bin_item(const Cx<T> *__restrict__ F, int64_t gs
             }
             const int total = __shfl_sync(0xffffffffu, inc, 31);
             if (total == 0) continue;
-            const int i1 = row ? (n1 < 0 ? n1 + ng : n1) : 0;
-            st.lo[lane] = l_lo;
-            st.pre[lane] = inc - len;
-            st.n1[lane] = n1;
-            st.row[lane] = (static_cast<int64_t>(i0) * ng + i1) * nh;
-            st.g[lane] = row ? g0 * gf[i1] : T(0);
+            const int pre = inc - len;
+            const unsigned nonempty = __ballot_sync(0xffffffffu, len > 0);
+            if (len > 0) {  // compacted: the k-th non-empty row at index k
+                const int i1 = n1 < 0 ? n1 + ng : n1;
+                int w;
+                if constexpr (sizeof(T) == 4) w = static_cast<int>(__float_as_uint(g0 * gf[i1]));
+                else w = i1;
+                st.rows[__popc(nonempty & ((1u << lane) - 1u))] = make_int4(pre, l_lo, n1, w);
+            }
             __syncwarp();
-            for (int m = lane; m < total; m += 32) {
-                // the row holding the m-th mode: the last row starting at or before m
-                // (an empty row starts where the next one does, which is then taken)
-                int j = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1)
-                    if (st.pre[j + step] <= m) j += step;
-                const int l = st.lo[j] + (m - st.pre[j]);
-                const int64_t mi = st.row[j] + l;
+            for (int m0 = 0; m0 < total; m0 += 32) {
+                // the row holding mode m = m0 + lane: non-empty rows start at increasing
+                // positions, so it is the last one starting at or before m: count the rows
+                // started before this window of 32 modes and the starts in it up to m
+                const bool in_win = len > 0 && pre >= m0 && pre < m0 + 32;
+                const unsigned starts = __reduce_or_sync(0xffffffffu, in_win ? 1u << (pre - m0) : 0u);
+                const int before = __popc(__ballot_sync(0xffffffffu, len > 0 && pre < m0));
+                const int m = m0 + lane;
+                if (m >= total) break;
+                const int q = before + __popc(starts & (0xffffffffu >> (31 - lane))) - 1;
+                const int4 rw = st.rows[q];
+                const int l = rw.y + (m - rw.x);
+                const int rn1 = rw.z, ri1 = rn1 < 0 ? rn1 + ng : rn1;
+                const int64_t mi = (static_cast<int64_t>(i0) * ng + ri1) * nh + l;
                 if (!PK_IN(mi, gstride, kChkMode) || !PK_IN(l, nh, kChkMode)) continue;
-                const T g = st.g[j] * gh[l] * ((l == 0 || l == nh - 1) ? T(1) : T(2));
+                T grow;
+                if constexpr (sizeof(T) == 4) grow = __uint_as_float(static_cast<unsigned>(rw.w));
+                else grow = g0 * gf[ri1];
+                const T g = grow * gh[l] * ((l == 0 || l == nh - 1) ? T(1) : T(2));
                 const Cx<T> d = F[mi], p0 = F[gstride + mi], p1 = F[2 * gstride + mi], p2 = F[3 * gstride + mi];
-                const T fn0 = static_cast<T>(n0), fn1 = static_cast<T>(st.n1[j]), fn2 = static_cast<T>(l);
+                const T fn0 = static_cast<T>(n0), fn1 = static_cast<T>(rn1), fn2 = static_cast<T>(l);
                 const T kr = fn0 * p0.x + fn1 * p1.x + fn2 * p2.x;
                 const T ki = fn0 * p0.y + fn1 * p1.y + fn2 * p2.y;
                 const Cx<T> q0{p0.x - vb0 * d.x, p0.y - vb0 * d.y};
@@ -312,66 +371,90 @@ __device__ __forceinline__ void bin_item(const Cx<T> *__restrict__ F, int64_t gs
             __syncwarp();
         }
     }
+    static_assert(kBinVals <= 8, "the reduce-scatter sums 8 values");
+    T hi[8], lo[8];
 #pragma unroll
-    for (int k = 0; k < kBinVals; ++k) {
-        const double dsum = warp_sum_pair(s[k], -c[k]);
-        if (lane == 0) partials[static_cast<int64_t>(item) * kBinVals + k] = dsum;
-    }
+    for (int k = 0; k < 8; ++k) hi[k] = k < kBinVals ? s[k] : T(0), lo[k] = k < kBinVals ? -c[k] : T(0);
+    const double dsum = warp_scatter_sum8(hi, lo);
+    const int k = (lane >> 2) & 7;
+    if ((lane & 3) == 0 && k < kBinVals) partials[static_cast<int64_t>(item) * kBinVals + k] = dsum;
 }
 
+// Warps draw items from a device counter, one at a time (taking the next index before
+// finishing the current item measured slower), in the order of the table's list of
+// non-empty items, so the large items of the central slabs are spread first and the
+// small ones fill the tail. Which warp takes an item does not change its result. The
+// last block to finish sets the counter back to zero for the next launch.
 template <typename T>
 __global__ void __launch_bounds__(kBinThreads, sizeof(T) == 4 ? 4 : 2)
 k_bin_shells(const Cx<T> *__restrict__ F, int64_t gstride, int ng, int nbins, const int *__restrict__ thresh,
              const T *__restrict__ gf, const T *__restrict__ gh, const double *__restrict__ mom,
+             const uint32_t *__restrict__ order, int nwork, unsigned *__restrict__ counter,
              double *__restrict__ partials)
 {
     constexpr int NW = kBinThreads / 32;
-    __shared__ BinWarpStage<T> s_st[NW];
+    __shared__ BinWarpStage s_st[NW];
     const double Mtot = mom[0];
     const T vb0 = static_cast<T>(mom[2] / Mtot), vb1 = static_cast<T>(mom[3] / Mtot), vb2 = static_cast<T>(mom[4] / Mtot);
-    const int w = threadIdx.x >> 5;
-    const int nwarps = gridDim.x * NW;
-    const int nitems = ng * nbins;
-    for (int item = blockIdx.x * NW + w; item < nitems; item += nwarps)
-        bin_item<T>(F, gstride, ng, nbins, thresh, gf, gh, vb0, vb1, vb2, partials, item, s_st[w]);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned j = 0;
+        if (lane == 0) j = atomicAdd(counter, 1u);
+        j = __shfl_sync(0xffffffffu, j, 0);
+        if (j >= static_cast<unsigned>(nwork)) break;
+        bin_item<T>(F, gstride, ng, nbins, thresh, gf, gh, vb0, vb1, vb2, partials, static_cast<int>(order[j]),
+                    s_st[w]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && atomicAdd(counter + 1, 1u) == gridDim.x - 1) counter[0] = 0u, counter[1] = 0u;
 }
 
-// Persistent form over the items of many FP32 catalogues (the batched estimate): warp
-// k of the grid takes the global items k, k + (warps), ...; each item is written to its
-// own catalogue's partials, so the results do not depend on which warp took it.
+// Persistent form over the non-empty items of many FP32 catalogues (the batched
+// estimate), drawn from one counter in catalogue order; each item is written to its own
+// catalogue's partials, so the results do not depend on which warp took it.
 __global__ void __launch_bounds__(kBinThreads, 4)
 k_bin_batch(const BinBatch jobs)
 {
     constexpr int NW = kBinThreads / 32;
-    __shared__ BinWarpStage<float> s_st[NW];
-    const int w = threadIdx.x >> 5;
-    const long long nwarps = static_cast<long long>(gridDim.x) * NW;
-    int j = 0;
-    for (long long item = static_cast<long long>(blockIdx.x) * NW + w; item < jobs.total_items; item += nwarps) {
-        while (j + 1 < jobs.n && jobs.job[j + 1].first_item <= item) ++j;
-        const BinJob &jb = jobs.job[j];
+    __shared__ BinWarpStage s_st[NW];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int jj = 0;
+    for (;;) {
+        unsigned nx = 0;
+        if (lane == 0) nx = atomicAdd(jobs.counter, 1u);
+        const long long item = __shfl_sync(0xffffffffu, nx, 0);
+        if (item >= jobs.total_items) break;
+        while (jj + 1 < jobs.n && jobs.job[jj + 1].first_item <= item) ++jj;  // items only grow
+        const BinJob &jb = jobs.job[jj];
         const double Mtot = jb.mom[0];
         const float vb0 = static_cast<float>(jb.mom[2] / Mtot), vb1 = static_cast<float>(jb.mom[3] / Mtot),
                     vb2 = static_cast<float>(jb.mom[4] / Mtot);
         const int nh = jb.ng / 2 + 1;
         const int64_t gstride = static_cast<int64_t>(jb.ng) * jb.ng * nh;
         bin_item<float>(static_cast<const Cx<float> *>(jb.grids), gstride, jb.ng, jb.nbins, jb.thresh, jb.gf, jb.gh,
-                        vb0, vb1, vb2, jb.partials, static_cast<int>(item - jb.first_item), s_st[w]);
+                        vb0, vb1, vb2, jb.partials, static_cast<int>(jb.order[item - jb.first_item]), s_st[w]);
     }
 }
 
 // out[k * nbins + b] = sum over slabs j of partials[(j * nbins + b) * NV + k], fixed order.
+// With thresh (the shell-major binning), the slabs that shell b misses hold no modes and
+// are skipped: their partials are never written.
 template <int NV>
 __global__ void __launch_bounds__(256)
-k_reduce_items(const double *__restrict__ partials, int nslabs, int nbins, double *__restrict__ out)
+k_reduce_items(const double *__restrict__ partials, int nslabs, int nbins, double *__restrict__ out,
+               const int *__restrict__ thresh = nullptr)
 {
     const int b = blockIdx.x;
     double s[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) s[k] = 0.0;
-    for (int j = threadIdx.x; j < nslabs; j += blockDim.x)
+    const int hi2 = thresh ? thresh[b + 1] : 0, lo2 = thresh ? thresh[b] : 0;
+    for (int j = threadIdx.x; j < nslabs; j += blockDim.x) {
+        const int n0 = j < nslabs / 2 ? j : j - nslabs;
+        if (thresh && (hi2 <= lo2 || hi2 - 1 - n0 * n0 < 0)) continue;
 #pragma unroll
         for (int k = 0; k < NV; ++k) s[k] += partials[(static_cast<int64_t>(j) * nbins + b) * NV + k];
+    }
     __shared__ double red[NV][256];
 #pragma unroll
     for (int k = 0; k < NV; ++k) red[k][threadIdx.x] = s[k];
@@ -590,6 +673,8 @@ void free_spectra_tables(SpectraTables &t)
     cudaFree(t.mode_sums);
     cudaFree(t.partials);
     cudaFree(t.item_partials);
+    cudaFree(t.bin_order);
+    cudaFree(t.bin_counter);
     t = SpectraTables{};
 }
 
@@ -670,8 +755,24 @@ cudaError_t build_spectra_tables(SpectraTables &t, int ng, int order, bool direc
     if ((e = cudaMalloc(reinterpret_cast<void **>(&t.item_partials),
                         static_cast<size_t>(ng) * nbins * kBinVals * sizeof(double))) != cudaSuccess)
         return e;
-    t.shell_blocks = num_sms * 8;
-    t.bytes = bintab.size() * sizeof(uint16_t) + thresh.size() * sizeof(int) +
+    // the non-empty (slab, shell) items (the same test as bin_item's), slabs by increasing
+    // |n0| (0, -1, 1, -2, ...), the outer shells of a slab first
+    std::vector<uint32_t> work;
+    for (int r = 0; r < ng; ++r) {
+        const int k = r >> 1, i0 = (r & 1) ? ng - 1 - k : k;
+        const int n0 = i0 < ng / 2 ? i0 : i0 - ng;
+        for (int b = nbins - 1; b >= 0; --b)
+            if (thresh[b + 1] > thresh[b] && thresh[b + 1] - 1 - n0 * n0 >= 0)
+                work.push_back(static_cast<uint32_t>(i0) * nbins + b);
+    }
+    t.bin_nwork = static_cast<int>(work.size());
+    if (work.empty()) work.push_back(0);  // keep a valid allocation
+    if ((e = upload(reinterpret_cast<void **>(&t.bin_order), work)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(reinterpret_cast<void **>(&t.bin_counter), 2 * sizeof(unsigned))) != cudaSuccess) return e;
+    if ((e = cudaMemset(t.bin_counter, 0, 2 * sizeof(unsigned))) != cudaSuccess) return e;
+    t.shell_blocks = num_sms * 4;  // resident blocks (56 registers, 256 threads)
+    t.bytes = work.size() * sizeof(uint32_t) + 2 * sizeof(unsigned) + bintab.size() * sizeof(uint16_t) +
+              thresh.size() * sizeof(int) +
               static_cast<size_t>(ng + nh) * (prec == PKMOM_F32 ? sizeof(float) : sizeof(double)) +
               static_cast<size_t>(ng + nh) * sizeof(double) +
               static_cast<size_t>(t.bin_blocks) * kModeVals * nbins * sizeof(double) +
@@ -727,14 +828,15 @@ cudaError_t launch_bin_shells(const SpectraTables &t, const void *grids, const d
     if (t.prec == PKMOM_F32)
         k_bin_shells<float><<<blocks, kBinThreads, 0, s>>>(
             static_cast<const Cx<float> *>(grids), gstride, ng, t.nbins, t.thresh,
-            static_cast<const float *>(t.g_full), static_cast<const float *>(t.g_half), moments_dev, t.item_partials);
+            static_cast<const float *>(t.g_full), static_cast<const float *>(t.g_half), moments_dev, t.bin_order,
+            t.bin_nwork, t.bin_counter, t.item_partials);
     else
         k_bin_shells<double><<<blocks, kBinThreads, 0, s>>>(
             static_cast<const Cx<double> *>(grids), gstride, ng, t.nbins, t.thresh,
-            static_cast<const double *>(t.g_full), static_cast<const double *>(t.g_half), moments_dev,
-            t.item_partials);
+            static_cast<const double *>(t.g_full), static_cast<const double *>(t.g_half), moments_dev, t.bin_order,
+            t.bin_nwork, t.bin_counter, t.item_partials);
     double *sums = t.mode_sums + static_cast<size_t>(kModeVals) * t.nbins;
-    k_reduce_items<kBinVals><<<t.nbins, 256, 0, s>>>(t.item_partials, ng, t.nbins, sums);
+    k_reduce_items<kBinVals><<<t.nbins, 256, 0, s>>>(t.item_partials, ng, t.nbins, sums, t.thresh);
     st.launches += 2;
     return cudaGetLastError();
 }
@@ -764,20 +866,24 @@ cudaError_t launch_bin_batch(BinBatch &batch, const SpectraTables *const *tables
 {
     long long first = 0;
     for (int k = 0; k < batch.n; ++k) {
+        batch.job[k].order = tables[k]->bin_order;
+        batch.job[k].nwork = tables[k]->bin_nwork;
         batch.job[k].first_item = first;
-        first += static_cast<long long>(batch.job[k].ng) * batch.job[k].nbins;
+        first += tables[k]->bin_nwork;
     }
     batch.total_items = first;
-    if (first == 0) return cudaSuccess;
-    const long long want = (first + kBinThreads / 32 - 1) / (kBinThreads / 32);
-    const unsigned blocks = static_cast<unsigned>(std::min<long long>(want, static_cast<long long>(num_sms) * 8));
-    k_bin_batch<<<blocks, kBinThreads, 0, s>>>(batch);
-    st.launches++;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
+    if (first > 0) {
+        const long long want = (first + kBinThreads / 32 - 1) / (kBinThreads / 32);
+        const unsigned blocks = static_cast<unsigned>(std::min<long long>(want, static_cast<long long>(num_sms) * 4));
+        if ((e = cudaMemsetAsync(batch.counter, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+        k_bin_batch<<<blocks, kBinThreads, 0, s>>>(batch);
+        st.launches++;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     for (int k = 0; k < batch.n; ++k) {
         const BinJob &jb = batch.job[k];
-        k_reduce_items<kBinVals><<<jb.nbins, 256, 0, s>>>(jb.partials, jb.ng, jb.nbins, sums_of[k]);
+        k_reduce_items<kBinVals><<<jb.nbins, 256, 0, s>>>(jb.partials, jb.ng, jb.nbins, sums_of[k], jb.thresh);
         st.launches++;
         if ((e = finalize_sums(*tables[k], *params[k], jb.mom, sums_of[k], out[k], s, st)) != cudaSuccess) return e;
     }
@@ -1254,7 +1360,7 @@ cudaError_t launch_spectra_mu(const SpectraTables &t, const pkmom_params &p, con
 {
     const int ng = t.ng, nh = ng / 2 + 1;
     const int64_t gstride = static_cast<int64_t>(ng) * ng * nh;
-    const unsigned blocks = static_cast<unsigned>(t.shell_blocks);
+    const unsigned blocks = static_cast<unsigned>(t.shell_blocks) * 2u;  // 8 blocks per SM
     const double d0 = dir ? dir[0] : 0.0, d1 = dir ? dir[1] : 0.0, d2 = dir ? dir[2] : 0.0;
     const int bulk_dir = dir ? 0 : 1;
     if (t.prec == PKMOM_F32)
