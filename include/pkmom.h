@@ -39,7 +39,10 @@
  * void*; NULL = legacy default stream) unless stated. Argument errors are
  * returned synchronously; a device-side error (a non-finite position) is latched
  * in the context and returned by pkmom_sync or by the next synchronising call.
- * A context is used from one host thread at a time.
+ * A context is used from one host thread at a time, and the work it queues must not
+ * overlap on the GPU across streams: its cached per-grid tables hold the binning's
+ * work counters and per-item partial sums (order such calls on one stream, or use
+ * one context per stream; pkmom_estimate_host_async overlaps only its own copies).
  */
 #ifndef PKMOM_H
 #define PKMOM_H

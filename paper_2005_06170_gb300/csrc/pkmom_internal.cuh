@@ -160,7 +160,9 @@ struct SpectraTables {
     // (the larger items first); items missing from it are empty and never written
     uint32_t *bin_order = nullptr;
     int bin_nwork = 0;
-    unsigned *bin_counter = nullptr;  // [2]: next entry of bin_order, blocks done (zero between launches)
+    // next entry of bin_order and blocks done: [0, 2) for k_bin_shells, [2, 4) for k_bin_mu
+    // (zero between launches)
+    unsigned *bin_counter = nullptr;
     size_t bytes = 0;            // device bytes of all the arrays above
 };
 cudaError_t build_spectra_tables(SpectraTables &t, int ng, int order, bool direct, int nbins, double umin,

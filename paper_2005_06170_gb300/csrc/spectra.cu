@@ -167,32 +167,6 @@ k_bin(const Cx<T> *__restrict__ F, int64_t gstride, int ng, uint32_t nmodes, con
     for (int k = threadIdx.x; k < kBinVals * nbins; k += blockDim.x) out[k] = s_bins[k];
 }
 
-// Warp sum of the lanes' values hi + lo, returned as FP64 (the same on every lane, fixed
-// butterfly order). For FP32 the partial sums are carried as unevaluated pairs of
-// floats with error-free two-sums at each level (FP64 adds are scarce on this part);
-// for FP64 plain adds.
-__device__ __forceinline__ double warp_sum_pair(float hi, float lo)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float bh = __shfl_xor_sync(0xffffffffu, hi, o), bl = __shfl_xor_sync(0xffffffffu, lo, o);
-        const float sh = __fadd_rn(hi, bh);  // two-sum: sh + se = hi + bh exactly
-        const float bb = __fsub_rn(sh, hi);
-        const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(sh, bb)), __fsub_rn(bh, bb));
-        const float t = __fadd_rn(se, __fadd_rn(lo, bl));
-        hi = __fadd_rn(sh, t);  // renormalise
-        lo = __fsub_rn(t, __fsub_rn(hi, sh));
-    }
-    return static_cast<double>(hi) + static_cast<double>(lo);
-}
-__device__ __forceinline__ double warp_sum_pair(double hi, double lo)
-{
-    double v = hi + lo;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // (hi, lo) += (bh, bl) for unevaluated float pairs: a two-sum of the high parts, then
 // the low parts and the rounding error added and renormalised.
 __device__ __forceinline__ void pair_add(float &hi, float &lo, float bh, float bl)
@@ -204,7 +178,11 @@ __device__ __forceinline__ void pair_add(float &hi, float &lo, float bh, float b
     hi = __fadd_rn(sh, t);
     lo = __fsub_rn(t, __fsub_rn(hi, sh));
 }
-__device__ __forceinline__ void pair_add(double &hi, double &lo, double bh, double bl) { hi += bh + bl, lo = 0.0; }
+__device__ __forceinline__ void pair_add(double &hi, double &lo, double bh, double bl)
+{
+    hi = (hi + lo) + (bh + bl);  // FP64: plain adds
+    lo = 0.0;
+}
 
 // Warp sums of 8 values per lane (value k as the pair hi[k] + lo[k]) by reduce-scatter:
 // at the steps across lanes 16, 8 and 4 apart each lane keeps half of the values it
@@ -437,18 +415,19 @@ k_bin_batch(const BinBatch jobs)
 }
 
 // out[k * nbins + b] = sum over slabs j of partials[(j * nbins + b) * NV + k], fixed order.
-// With thresh (the shell-major binning), the slabs that shell b misses hold no modes and
-// are skipped: their partials are never written.
+// With thresh: column b belongs to shell b / per_shell, and the slabs that shell misses
+// hold no modes and are skipped (their partials are never written).
 template <int NV>
 __global__ void __launch_bounds__(256)
 k_reduce_items(const double *__restrict__ partials, int nslabs, int nbins, double *__restrict__ out,
-               const int *__restrict__ thresh = nullptr)
+               const int *__restrict__ thresh = nullptr, int per_shell = 1)
 {
     const int b = blockIdx.x;
     double s[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) s[k] = 0.0;
-    const int hi2 = thresh ? thresh[b + 1] : 0, lo2 = thresh ? thresh[b] : 0;
+    const int sh = b / per_shell;
+    const int hi2 = thresh ? thresh[sh + 1] : 0, lo2 = thresh ? thresh[sh] : 0;
     for (int j = threadIdx.x; j < nslabs; j += blockDim.x) {
         const int n0 = j < nslabs / 2 ? j : j - nslabs;
         if (thresh && (hi2 <= lo2 || hi2 - 1 - n0 * n0 < 0)) continue;
@@ -768,10 +747,10 @@ cudaError_t build_spectra_tables(SpectraTables &t, int ng, int order, bool direc
     t.bin_nwork = static_cast<int>(work.size());
     if (work.empty()) work.push_back(0);  // keep a valid allocation
     if ((e = upload(reinterpret_cast<void **>(&t.bin_order), work)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(reinterpret_cast<void **>(&t.bin_counter), 2 * sizeof(unsigned))) != cudaSuccess) return e;
-    if ((e = cudaMemset(t.bin_counter, 0, 2 * sizeof(unsigned))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(reinterpret_cast<void **>(&t.bin_counter), 4 * sizeof(unsigned))) != cudaSuccess) return e;
+    if ((e = cudaMemset(t.bin_counter, 0, 4 * sizeof(unsigned))) != cudaSuccess) return e;
     t.shell_blocks = num_sms * 4;  // resident blocks (56 registers, 256 threads)
-    t.bytes = work.size() * sizeof(uint32_t) + 2 * sizeof(unsigned) + bintab.size() * sizeof(uint16_t) +
+    t.bytes = work.size() * sizeof(uint32_t) + 4 * sizeof(unsigned) + bintab.size() * sizeof(uint16_t) +
               thresh.size() * sizeof(int) +
               static_cast<size_t>(ng + nh) * (prec == PKMOM_F32 ? sizeof(float) : sizeof(double)) +
               static_cast<size_t>(ng + nh) * sizeof(double) +
@@ -1147,7 +1126,8 @@ __global__ void __launch_bounds__(kBinThreads, 2)
 k_bin_mu(const Cx<T> *__restrict__ F, int64_t gstride, int ng, int nbins, int nmu, const int *__restrict__ thresh,
          const T *__restrict__ gf, const T *__restrict__ gh, const double *__restrict__ hf,
          const double *__restrict__ hh, const double *__restrict__ mom, double ge0, double ge1, double ge2,
-         int bulk_dir, double *__restrict__ partials)
+         int bulk_dir, const uint32_t *__restrict__ order, int nwork, unsigned *__restrict__ counter,
+         double *__restrict__ partials)
 {
     constexpr int NW = kBinThreads / 32;
     __shared__ int s_lo[NW][32], s_pre[NW][32], s_n1[NW][32];
@@ -1171,9 +1151,15 @@ k_bin_mu(const Cx<T> *__restrict__ F, int64_t gstride, int ng, int nbins, int nm
     const float e0 = static_cast<float>(ed0), e1 = static_cast<float>(ed1), e2 = static_cast<float>(ed2);
     const T et0 = static_cast<T>(ed0), et1 = static_cast<T>(ed1), et2 = static_cast<T>(ed2);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int nwarps = gridDim.x * NW;
-    const int nitems = ng * nbins * nmu;
-    for (int item = blockIdx.x * NW + w; item < nitems; item += nwarps) {
+    // items (slab, shell, mu bin) of the (slab, shell) pairs that hold modes, drawn from a
+    // device counter; the last block sets it back to zero
+    const unsigned nitems = static_cast<unsigned>(nwork) * static_cast<unsigned>(nmu);
+    for (;;) {
+        unsigned jw = 0;
+        if (lane == 0) jw = atomicAdd(counter, 1u);
+        jw = __shfl_sync(0xffffffffu, jw, 0);
+        if (jw >= nitems) break;
+        const int item = static_cast<int>(order[jw / nmu]) * nmu + static_cast<int>(jw % nmu);
         const int m = item % nmu;
         const int b = (item / nmu) % nbins;
         const int i0 = item / (nmu * nbins);
@@ -1183,7 +1169,11 @@ k_bin_mu(const Cx<T> *__restrict__ F, int64_t gstride, int ng, int nbins, int nm
 #pragma unroll
         for (int k = 0; k < kMuVals; ++k) s[k] = T(0), c[k] = T(0);
         const int rem = hi2 - 1 - n0 * n0;
-        if (i0 != ng / 2 && hi2 > lo2 && rem >= 0) {
+        if (i0 == ng / 2 || hi2 <= lo2 || rem < 0) {  // no mode: zero sums, no reduction
+            if (lane < kMuVals) partials[static_cast<int64_t>(item) * kMuVals + lane] = 0.0;
+            continue;
+        }
+        {
             const int R1 = isqrt_floor(rem);
             const int n1lo = max(1 - ng / 2, -R1), n1hi = min(ng / 2 - 1, R1);
             const T g0 = gf[i0];
@@ -1282,11 +1272,21 @@ k_bin_mu(const Cx<T> *__restrict__ F, int64_t gstride, int ng, int nbins, int nm
             }
         }
 #pragma unroll
-        for (int k = 0; k < kMuVals; ++k) {
-            const double dsum = warp_sum_pair(s[k], -c[k]);
-            if (lane == 0) partials[static_cast<int64_t>(item) * kMuVals + k] = dsum;
+        for (int g = 0; g < (kMuVals + 7) / 8; ++g) {  // reduce-scatter, 8 sums at a time
+            T hi[8], lo[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int v = 8 * g + k;
+                hi[k] = v < kMuVals ? s[v] : T(0);
+                lo[k] = v < kMuVals ? -c[v] : T(0);
+            }
+            const double dsum = warp_scatter_sum8(hi, lo);
+            const int v = 8 * g + ((lane >> 2) & 7);
+            if ((lane & 3) == 0 && v < kMuVals) partials[static_cast<int64_t>(item) * kMuVals + v] = dsum;
         }
     }
+    __syncthreads();
+    if (threadIdx.x == 0 && atomicAdd(counter + 1, 1u) == gridDim.x - 1) counter[0] = 0u, counter[1] = 0u;
 }
 
 struct MuParams {
@@ -1360,21 +1360,21 @@ cudaError_t launch_spectra_mu(const SpectraTables &t, const pkmom_params &p, con
 {
     const int ng = t.ng, nh = ng / 2 + 1;
     const int64_t gstride = static_cast<int64_t>(ng) * ng * nh;
-    const unsigned blocks = static_cast<unsigned>(t.shell_blocks) * 2u;  // 8 blocks per SM
+    const unsigned blocks = static_cast<unsigned>(t.shell_blocks) / 2u;  // resident: 2 blocks per SM
     const double d0 = dir ? dir[0] : 0.0, d1 = dir ? dir[1] : 0.0, d2 = dir ? dir[2] : 0.0;
     const int bulk_dir = dir ? 0 : 1;
     if (t.prec == PKMOM_F32)
         k_bin_mu<float><<<blocks, kBinThreads, 0, s>>>(
             static_cast<const Cx<float> *>(grids), gstride, ng, t.nbins, nmu, t.thresh,
             static_cast<const float *>(t.g_full), static_cast<const float *>(t.g_half), t.h_full, t.h_half,
-            moments_dev, d0, d1, d2, bulk_dir, partials);
+            moments_dev, d0, d1, d2, bulk_dir, t.bin_order, t.bin_nwork, t.bin_counter + 2, partials);
     else
         k_bin_mu<double><<<blocks, kBinThreads, 0, s>>>(
             static_cast<const Cx<double> *>(grids), gstride, ng, t.nbins, nmu, t.thresh,
             static_cast<const double *>(t.g_full), static_cast<const double *>(t.g_half), t.h_full, t.h_half,
-            moments_dev, d0, d1, d2, bulk_dir, partials);
+            moments_dev, d0, d1, d2, bulk_dir, t.bin_order, t.bin_nwork, t.bin_counter + 2, partials);
     const int ncells = t.nbins * nmu;
-    k_reduce_items<kMuVals><<<ncells, 256, 0, s>>>(partials, ng, ncells, sums);
+    k_reduce_items<kMuVals><<<ncells, 256, 0, s>>>(partials, ng, ncells, sums, t.thresh, nmu);
     MuParams fp;
     fp.V = p.box_L * p.box_L * p.box_L;
     fp.kf = kTwoPi / p.box_L;
