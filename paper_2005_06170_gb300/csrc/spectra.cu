@@ -302,48 +302,69 @@ __device__ __forceinline__ void bin_item(const Cx<T> *__restrict__ F, int64_t gs
                 st.rows[__popc(nonempty & ((1u << lane) - 1u))] = make_int4(pre, l_lo, n1, w);
             }
             __syncwarp();
-            for (int m0 = 0; m0 < total; m0 += 32) {
-                // the row holding mode m = m0 + lane: non-empty rows start at increasing
-                // positions, so it is the last one starting at or before m: count the rows
-                // started before this window of 32 modes and the starts in it up to m
-                const bool in_win = len > 0 && pre >= m0 && pre < m0 + 32;
-                const unsigned starts = __reduce_or_sync(0xffffffffu, in_win ? 1u << (pre - m0) : 0u);
-                const int before = __popc(__ballot_sync(0xffffffffu, len > 0 && pre < m0));
-                const int m = m0 + lane;
-                if (m >= total) break;
-                const int q = before + __popc(starts & (0xffffffffu >> (31 - lane))) - 1;
-                const int4 rw = st.rows[q];
-                const int l = rw.y + (m - rw.x);
-                const int rn1 = rw.z, ri1 = rn1 < 0 ? rn1 + ng : rn1;
-                const int64_t mi = (static_cast<int64_t>(i0) * ng + ri1) * nh + l;
-                if (!PK_IN(mi, gstride, kChkMode) || !PK_IN(l, nh, kChkMode)) continue;
-                T grow;
-                if constexpr (sizeof(T) == 4) grow = __uint_as_float(static_cast<unsigned>(rw.w));
-                else grow = g0 * gf[ri1];
-                const T g = grow * gh[l] * ((l == 0 || l == nh - 1) ? T(1) : T(2));
-                const Cx<T> d = F[mi], p0 = F[gstride + mi], p1 = F[2 * gstride + mi], p2 = F[3 * gstride + mi];
-                const T fn0 = static_cast<T>(n0), fn1 = static_cast<T>(rn1), fn2 = static_cast<T>(l);
-                const T kr = fn0 * p0.x + fn1 * p1.x + fn2 * p2.x;
-                const T ki = fn0 * p0.y + fn1 * p1.y + fn2 * p2.y;
-                const Cx<T> q0{p0.x - vb0 * d.x, p0.y - vb0 * d.y};
-                const Cx<T> q1{p1.x - vb1 * d.x, p1.y - vb1 * d.y};
-                const Cx<T> q2{p2.x - vb2 * d.x, p2.y - vb2 * d.y};
-                const T jr = fn0 * q0.x + fn1 * q1.x + fn2 * q2.x;
-                const T ji = fn0 * q0.y + fn1 * q1.y + fn2 * q2.y;
-                T v[kBinVals];
-                v[0] = g * (d.x * d.x + d.y * d.y);
-                v[1] = g * (p0.x * p0.x + p0.y * p0.y + p1.x * p1.x + p1.y * p1.y + p2.x * p2.x + p2.y * p2.y);
-                v[2] = g * (kr * kr + ki * ki);
-                v[3] = g * (d.x * ki - d.y * kr);  // Im(conj(F_d) * (n.F_p))
-                v[4] = g * (q0.x * q0.x + q0.y * q0.y + q1.x * q1.x + q1.y * q1.y + q2.x * q2.x + q2.y * q2.y);
-                v[5] = g * (jr * jr + ji * ji);
-                v[6] = g * (d.x * ji - d.y * jr);
+            for (int m0 = 0; m0 < total; m0 += 64) {
+                // two windows of 32 modes per pass (8 loads in flight per lane); the row
+                // holding mode m = w0 + lane: non-empty rows start at increasing positions,
+                // so it is the last one starting at or before m: count the rows started
+                // before the window and the starts in it up to m
+                int mm[2], mlo[2], mn1[2];
+                int64_t mi[2];
+                bool ok[2];
+                T grow[2];
 #pragma unroll
-                for (int k = 0; k < kBinVals; ++k) {  // Kahan: s - c carries the sum
-                    const T y = v[k] - c[k];
-                    const T t = s[k] + y;
-                    c[k] = (t - s[k]) - y;
-                    s[k] = t;
+                for (int h = 0; h < 2; ++h) {
+                    const int w0 = m0 + 32 * h;
+                    const bool in_win = len > 0 && pre >= w0 && pre < w0 + 32;
+                    const unsigned starts = __reduce_or_sync(0xffffffffu, in_win ? 1u << (pre - w0) : 0u);
+                    const int before = __popc(__ballot_sync(0xffffffffu, len > 0 && pre < w0));
+                    mm[h] = w0 + lane;
+                    ok[h] = mm[h] < total;
+                    const int q = before + __popc(starts & (0xffffffffu >> (31 - lane))) - 1;
+                    const int4 rw = st.rows[ok[h] ? q : 0];
+                    mlo[h] = rw.y + (mm[h] - rw.x);
+                    mn1[h] = rw.z;
+                    const int ri1 = rw.z < 0 ? rw.z + ng : rw.z;
+                    mi[h] = (static_cast<int64_t>(i0) * ng + ri1) * nh + mlo[h];
+                    if (ok[h] && (!PK_IN(mi[h], gstride, kChkMode) || !PK_IN(mlo[h], nh, kChkMode))) ok[h] = false;
+                    if constexpr (sizeof(T) == 4) grow[h] = __uint_as_float(static_cast<unsigned>(rw.w));
+                    else grow[h] = g0 * gf[ri1];
+                }
+                Cx<T> dd[2], pp0[2], pp1[2], pp2[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (ok[h]) {
+                        dd[h] = F[mi[h]], pp0[h] = F[gstride + mi[h]], pp1[h] = F[2 * gstride + mi[h]],
+                        pp2[h] = F[3 * gstride + mi[h]];
+                    }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (!ok[h]) continue;
+                    const int l = mlo[h];
+                    const Cx<T> d = dd[h], p0 = pp0[h], p1 = pp1[h], p2 = pp2[h];
+                    const T g = grow[h] * gh[l] * ((l == 0 || l == nh - 1) ? T(1) : T(2));
+                    const T fn0 = static_cast<T>(n0), fn1 = static_cast<T>(mn1[h]), fn2 = static_cast<T>(l);
+                    const T kr = fn0 * p0.x + fn1 * p1.x + fn2 * p2.x;
+                    const T ki = fn0 * p0.y + fn1 * p1.y + fn2 * p2.y;
+                    const Cx<T> q0{p0.x - vb0 * d.x, p0.y - vb0 * d.y};
+                    const Cx<T> q1{p1.x - vb1 * d.x, p1.y - vb1 * d.y};
+                    const Cx<T> q2{p2.x - vb2 * d.x, p2.y - vb2 * d.y};
+                    const T jr = fn0 * q0.x + fn1 * q1.x + fn2 * q2.x;
+                    const T ji = fn0 * q0.y + fn1 * q1.y + fn2 * q2.y;
+                    T v[kBinVals];
+                    v[0] = g * (d.x * d.x + d.y * d.y);
+                    v[1] = g * (p0.x * p0.x + p0.y * p0.y + p1.x * p1.x + p1.y * p1.y + p2.x * p2.x + p2.y * p2.y);
+                    v[2] = g * (kr * kr + ki * ki);
+                    v[3] = g * (d.x * ki - d.y * kr);  // Im(conj(F_d) * (n.F_p))
+                    v[4] = g * (q0.x * q0.x + q0.y * q0.y + q1.x * q1.x + q1.y * q1.y + q2.x * q2.x + q2.y * q2.y);
+                    v[5] = g * (jr * jr + ji * ji);
+                    v[6] = g * (d.x * ji - d.y * jr);
+#pragma unroll
+                    for (int k = 0; k < kBinVals; ++k) {  // Kahan: s - c carries the sum
+                        const T y = v[k] - c[k];
+                        const T t = s[k] + y;
+                        c[k] = (t - s[k]) - y;
+                        s[k] = t;
+                    }
                 }
             }
             __syncwarp();
