@@ -1388,7 +1388,8 @@ k_deposit_fx_batch(const FxBatch jobs, unsigned long long *__restrict__ counter)
 //
 // Lane mapping: a warp takes a block of 2 x 4 cell columns; lane (x, y, m) takes the
 // first particles of cells z = 4m .. 4m + 3 of its column and sums their contributions
-// to each node column's 7 z nodes in registers before adding them (home_quad). The
+// to each node column's 7 z nodes in registers before adding them (home_quad), two
+// fields' roundings per paired FMA (fma.rn.f32x2, each half the scalar FMA's result). The
 // buffer's x pitch is 16 modulo 32 banks, its y pitch 19 and its z pitch 1, so the 32
 // lanes of every add hit 32 different banks (checked at compile time below): one
 // wavefront each. Particles beyond the first of a cell go to a per-warp queue and are
@@ -1540,6 +1541,23 @@ __device__ __forceinline__ void home_particle(int *acc, const Record<float> &r, 
 // exact. An empty cell has q = 0 and adds exactly the magic constant. With the lanes of
 // a warp on 2 x 4 columns (cx, cy) and m = 0..3, the 32 lanes of every add hit 32
 // different banks: (16 cx + 19 cy + 4 m) mod 32 is distinct over them.
+// Pairs of FP32 values in one 64-bit register pair for the paired FP32 FMA of sm_100
+// and later (fma.rn.f32x2: two correctly rounded FMAs per instruction issued, each the
+// same result as the scalar instruction).
+using f32x2 = unsigned long long;
+__device__ __forceinline__ f32x2 f2_pack(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 __device__ __forceinline__ void home_quad(unsigned acc_s, const Record<float> (&r)[4], const bool (&has)[4], int cx,
                                           int cy, int m, float sc0, float sc1, float sc2, float sc3)
 {
@@ -1557,6 +1575,10 @@ __device__ __forceinline__ void home_quad(unsigned acc_s, const Record<float> (&
         q[j][2] = has[j] ? r[j].q.z * sc2 : 0.0f;
         q[j][3] = has[j] ? r[j].q.w * sc3 : 0.0f;
     }
+    f32x2 qp[4][2];  // fields (0, 1) and (2, 3) of each cell as pairs
+#pragma unroll
+    for (int j = 0; j < 4; ++j) qp[j][0] = f2_pack(q[j][0], q[j][1]), qp[j][1] = f2_pack(q[j][2], q[j][3]);
+    const f32x2 mg = f2_pack(kMagic, kMagic);
     // buffer index of node (cx - 1 + dx, cy - 1 + dy, 4m - 1 + i) is (cx + dx) PX + (cy + dy) PY + 4m + i.
     // The 4 x 4 node columns are two rolled loops (a short body for the instruction
     // cache); the weights of the current dx and dy are kept in slot 0 by rotating them.
@@ -1580,8 +1602,12 @@ __device__ __forceinline__ void home_quad(unsigned acc_s, const Record<float> (&
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const float ww = w01 * wz[j][k];
-#pragma unroll
-                    for (int f = 0; f < 4; ++f) a[j + k][f] += __float_as_uint(fmaf(q[j][f], ww, kMagic));
+                    const f32x2 w2 = f2_pack(ww, ww);
+                    const f32x2 t01 = f2_fma(qp[j][0], w2, mg), t23 = f2_fma(qp[j][1], w2, mg);
+                    a[j + k][0] += static_cast<unsigned>(t01);
+                    a[j + k][1] += static_cast<unsigned>(t01 >> 32);
+                    a[j + k][2] += static_cast<unsigned>(t23);
+                    a[j + k][3] += static_cast<unsigned>(t23 >> 32);
                 }
             }
             const unsigned b = base + 4u * static_cast<unsigned>(dy * kHomePY);
