@@ -1531,16 +1531,6 @@ __device__ __forceinline__ void home_particle(int *acc, const Record<float> &r, 
     }
 }
 
-// The first particles of four z-consecutive home cells (z = 4m .. 4m + 3 of column
-// (cx, cy)) of one lane. For each of the 16 (x, y) stencil node columns the lane sums
-// the cells' contributions to the 7 z nodes it reaches in registers, then adds the 7
-// sums: 28 shared adds per node column instead of 64 for four particles one by one.
-// Each contribution is the same rounded integer as in home_particle (same products, one
-// FFMA against 1.5 * 2^23); the raw bit patterns are summed modulo 2^32 and the magic
-// constant is taken off once per node (cnt(i) cells reach z node i), so the sums are
-// exact. An empty cell has q = 0 and adds exactly the magic constant. With the lanes of
-// a warp on 2 x 4 columns (cx, cy) and m = 0..3, the 32 lanes of every add hit 32
-// different banks: (16 cx + 19 cy + 4 m) mod 32 is distinct over them.
 // Pairs of FP32 values in one 64-bit register pair for the paired FP32 FMA of sm_100
 // and later (fma.rn.f32x2: two correctly rounded FMAs per instruction issued, each the
 // same result as the scalar instruction).
@@ -1558,6 +1548,16 @@ __device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c)
     return d;
 }
 
+// The first particles of four z-consecutive home cells (z = 4m .. 4m + 3 of column
+// (cx, cy)) of one lane. For each of the 16 (x, y) stencil node columns the lane sums
+// the cells' contributions to the 7 z nodes it reaches in registers, then adds the 7
+// sums: 28 shared adds per node column instead of 64 for four particles one by one.
+// Each contribution is the same rounded integer as in home_particle (same products, one
+// FMA against 1.5 * 2^23, here two fields per paired FMA); the raw bit patterns are summed modulo 2^32 and the magic
+// constant is taken off once per node (cnt(i) cells reach z node i), so the sums are
+// exact. An empty cell has q = 0 and adds exactly the magic constant. With the lanes of
+// a warp on 2 x 4 columns (cx, cy) and m = 0..3, the 32 lanes of every add hit 32
+// different banks: (16 cx + 19 cy + 4 m) mod 32 is distinct over them.
 __device__ __forceinline__ void home_quad(unsigned acc_s, const Record<float> (&r)[4], const bool (&has)[4], int cx,
                                           int cy, int m, float sc0, float sc1, float sc2, float sc3)
 {
