@@ -58,7 +58,7 @@ DEFAULT = "zeldovich512_ng512"
 # capture of the current kernels; a stage whose kernels change drops its entry until
 # it is captured again
 MEASURED_TRAFFIC = {
-    ("zeldovich512_ng512", "deposit"): ((4905.6 + 3595.1 + 3714.8 + 1623.7) * 1e6,
+    ("zeldovich512_ng512", "deposit"): ((4981.8 + 3626.1 + 3716.0 + 1623.8) * 1e6,
                                         "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_deposit_home and "
                                         "k_home_fixup, mean of 5 launches of the 512^3 workload "
                                         "(profiles/launches_zeldovich512_ng512.md)"),
@@ -67,7 +67,7 @@ MEASURED_TRAFFIC = {
 # the current kernel on the 256^3 workload, scaled to other workloads by particle count
 # (the same work per particle at one particle per cell)
 MEASURED_INSTRUCTIONS = {
-    "k_deposit_home": (661.98e6, 256 ** 3, "ncu smsp__inst_executed.sum of k_deposit_home on the 256^3 workload "
+    "k_deposit_home": (596.13e6, 256 ** 3, "ncu smsp__inst_executed.sum of k_deposit_home on the 256^3 workload "
                                          "(profiles/kernels_zeldovich256_ng256.md), scaled by particles"),
 }
 # configs 4 and 5 run through their own drivers below
