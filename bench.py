@@ -17,6 +17,7 @@ own GPU (the estimate of one catalogue does not shard); the slowest rank's time 
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -368,8 +369,16 @@ def e2e_host(ctx, cat, p, stream, torch, k_pipe=30, k_single=7):
     hp = torch.from_numpy(cat["pos"]).pin_memory()
     hv = torch.from_numpy(cat["vel"]).pin_memory()
     pipe = HostPipeline(n_max=n, nbins_max=p.nbins, precision=p.precision)
-    pipe.submit(hp, hv, p).result()  # warm-up: plans, tables, buffers
+    # warm-up: plans, tables, buffers and both staging slots (the second is allocated by
+    # the second call)
+    for _ in range(2):
+        pipe.submit(hp, hv, p).result()
     torch.cuda.synchronize()
+    # the Python collector paused while the host loops are timed (as timeit does): a full
+    # collection of this process's objects takes about as long as several estimates
+    gc.collect()
+    gc_was = gc.isenabled()
+    gc.disable()
     t0 = time.perf_counter()
     prev = None
     done = []  # host time at which each step's result was in hand
@@ -392,11 +401,14 @@ def e2e_host(ctx, cat, p, stream, torch, k_pipe=30, k_single=7):
         t1 = time.perf_counter()
         ctx.estimate_host(hpn, hvn, p, out=hout, stream=stream)
         calls.append(time.perf_counter() - t1)
+    if gc_was:
+        gc.enable()
     dt1 = float(np.median(calls))  # a call now and then takes far longer on a shared host
     return {"value": n / dt, "unit": "particles/s", "h2d_bytes_per_step": int(hp.nbytes + hv.nbytes),
             "d2h_bytes_per_step": int(pkmom.NROWS * p.nbins * 8), "ms_per_step": dt * 1e3, "steps": k_pipe,
             "api": "pkmom_estimate_host_async + pkmom_wait (copy of step i+1 overlaps the estimate of step i)",
             "step_intervals_ms": {"median": float(np.median(gaps[1:]) * 1e3), "max": float(gaps.max() * 1e3),
+                                  "argmax": int(gaps.argmax()),
                                   "first": float(gaps[0] * 1e3),
                                   "note": "value is the mean over all steps; the first interval holds the "
                                           "first copy, which nothing overlaps"},
