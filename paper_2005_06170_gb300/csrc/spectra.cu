@@ -227,11 +227,12 @@ __device__ __forceinline__ int isqrt_floor(int x)
 // Shell-major binning. Work item (n0, b): all modes of shell b in the slab n_x = n0,
 // one warp per item, so each lane keeps one set of sums for the whole item. Items are
 // taken slab by slab, so the items running together read the same few slabs (which
-// stay in L2); items that hold no mode are not run. The shell is the integer interval thresh[b] <= |n|^2 < thresh[b + 1]; in each
-// row (n0, n1) its modes form one run of l, found with exact integer square roots (no
-// mode is tested against a table). The runs of 32 rows are laid end to end and the
-// warp walks the joined list 32 modes at a time (lane j takes the j-th mode), so all
-// lanes work and consecutive lanes read consecutive modes of a row. The seven per-mode
+// stay in L2); items that hold no mode are not run. The shell is the integer interval
+// thresh[b] <= |n|^2 < thresh[b + 1]; in each row (n0, n1) its modes form one run of l,
+// found with exact integer square roots (no mode is tested against a table). The runs
+// of 32 rows are laid end to end and the warp walks the joined list in windows of 32
+// modes, two windows per pass (lane j takes the j-th mode of each), so all lanes work
+// and consecutive lanes read consecutive modes of a row. The seven per-mode
 // values are summed with Kahan-compensated adds in the grid precision; one warp
 // reduce-scatter per item (float pairs for FP32) writes partials[item][kBinVals] in FP64,
 // and k_reduce_items adds the items of each shell in a fixed order.
