@@ -63,6 +63,13 @@ MEASURED_TRAFFIC = {
                                         "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_deposit_home and "
                                         "k_home_fixup, mean of 5 launches of the 512^3 workload "
                                         "(profiles/launches_zeldovich512_ng512.md)"),
+    # the same density (1/8 particle per cell) captured at 256^3 particles on 512^3 and
+    # scaled by 8: the records read, the key rows read and the grid written all grow with
+    # the particles and cells, which are both 8 times as many
+    ("zeldovich512_ng1024", "deposit"): (8 * (1.27 + 2.11) * 1e9,
+                                         "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_deposit_fx "
+                                         "launch on 256^3 particles and a 512^3 grid "
+                                         "(profiles/deposit_sparse_zeldovich256_ng512.md), times 8"),
 }
 # warp instructions per launch of the dominant kernel, from one ncu --set full capture of
 # the current kernel on the 256^3 workload, scaled to other workloads by particle count
