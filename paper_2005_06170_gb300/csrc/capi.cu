@@ -22,7 +22,13 @@ struct PlanEntry {
     int ng, prec;
     cufftHandle h;
     size_t work;  // bytes of the workspace cuFFT allocated for the plan
+    int batch;    // grids per execution: 4 (the whole set) for small grids, else 1
 };
+
+// Grids up to this size are transformed four at a time by one plan: at 128^3 a plan
+// over the four grids took half the time per grid of one grid per plan (measured; from
+// 256^3 on the time per grid was the same either way).
+constexpr int kFftBatchMaxNg = 128;
 
 struct TimedEvent {
     int stage;
@@ -278,12 +284,13 @@ pkmom_status get_plan(pkmom_ctx *ctx, int ng, int prec, cufftHandle *out)
     const long long idist = 1LL * ng * ng * (ng + 2);
     const long long odist = 1LL * ng * ng * (ng / 2 + 1);
     size_t work = 0;
+    // larger grids: one grid per plan, executed four times (a batch of four 1024^3 grids
+    // made cuFFT allocate a 17 GB workspace and run twice as long, measured)
+    const int batch = ng <= kFftBatchMaxNg ? 4 : 1;
     cufftResult r = cufftCreate(&h);
     if (r == CUFFT_SUCCESS) {
-        // one grid per plan, executed four times: a batch of four 1024^3 grids made
-        // cuFFT allocate a 17 GB workspace and run twice as long (measured)
         r = cufftMakePlanMany64(h, 3, n, inembed, 1, idist, onembed, 1, odist,
-                                prec == PKMOM_F32 ? CUFFT_R2C : CUFFT_D2Z, 1, &work);
+                                prec == PKMOM_F32 ? CUFFT_R2C : CUFFT_D2Z, batch, &work);
         if (r != CUFFT_SUCCESS) cufftDestroy(h);
     }
     if (r != CUFFT_SUCCESS) {
@@ -291,7 +298,7 @@ pkmom_status get_plan(pkmom_ctx *ctx, int ng, int prec, cufftHandle *out)
         std::snprintf(buf, sizeof buf, "cufftPlanMany(ng=%d) failed with code %d", ng, int(r));
         return fail(ctx, r == CUFFT_ALLOC_FAILED ? PKMOM_ENOMEM : PKMOM_ECUFFT, buf);
     }
-    ctx->plans.push_back({ng, prec, h, work});
+    ctx->plans.push_back({ng, prec, h, work, batch});
     *out = h;
     return PKMOM_OK;
 }
@@ -522,8 +529,9 @@ size_t pkmom_footprint_bytes(const pkmom_params *p, int64_t n)
     const size_t elem = p->precision == PKMOM_F64 ? 8 : 4;
     const size_t grids = pkmom_grid_bytes(p->ng, p->precision);
     const size_t staging = size_t(n) * 7 * elem;
-    // cuFFT's in-place workspace is at most one grid's worth
-    return grids + grids / 4 + pkmom_assign_scratch_bytes(p, n) + staging + (size_t(64) << 10);
+    // cuFFT's in-place workspace: at most one grid's worth per grid in the plan's batch
+    const size_t fft_work = p->ng <= kFftBatchMaxNg ? grids : grids / 4;
+    return grids + fft_work + pkmom_assign_scratch_bytes(p, n) + staging + (size_t(64) << 10);
 }
 
 pkmom_status pkmom_assign(pkmom_ctx *ctx, const pkmom_catalog *cat, const pkmom_params *p, void *grids,
@@ -574,7 +582,8 @@ pkmom_status pkmom_fft(pkmom_ctx *ctx, const pkmom_params *p, void *grids, void 
     if (cufftSetStream(h, st) != CUFFT_SUCCESS) return fail(ctx, PKMOM_ECUFFT, "cufftSetStream failed");
     StageTimer t(ctx, PKMOM_STAGE_FFT, st);
     const size_t gelems = size_t(p->ng) * p->ng * (p->ng + 2);
-    for (int f = 0; f < 4; ++f) {
+    const int execs = p->ng <= kFftBatchMaxNg ? 1 : 4;  // the plan's batch covers 4 / execs grids
+    for (int f = 0; f < execs; ++f) {
         cufftResult r;
         if (p->precision == PKMOM_F32) {
             auto *g = static_cast<cufftReal *>(grids) + f * gelems;
