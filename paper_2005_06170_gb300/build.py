@@ -35,7 +35,7 @@ def sources() -> list[str]:
 
 
 def _deps() -> list[str]:
-    return sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")] + \
+    return sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + \
         [os.path.join(ROOT, "include", "pkmom.h")]
 
 

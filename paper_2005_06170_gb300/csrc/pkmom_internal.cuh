@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "../../include/pkmom.h"
+#include "shells.h"
 
 // Checked builds (compiled with -DPKMOM_CHECKED=1 into libpkmom_checked.so): every
 // grid, halo, shared-buffer, sort-key, record and bin index is tested before its access;

@@ -690,16 +690,9 @@ cudaError_t build_spectra_tables(SpectraTables &t, int ng, int order, bool direc
     t.umax = umax;
     t.prec = prec;
     const int nh = ng / 2 + 1;
-    // shells: the same FP64 expression as the definition of the bins
-    t.nsq_max = static_cast<int>(std::floor(umax * umax)) + 1;
-    std::vector<uint16_t> bintab(t.nsq_max + 1, 0xffff);
-    for (int nsq = 1; nsq <= t.nsq_max; ++nsq) {
-        const double u = std::sqrt(static_cast<double>(nsq));
-        if (u < umin || u > umax) continue;
-        double tb = std::floor(((u - umin) * nbins) / (umax - umin));
-        if (tb > nbins - 1) tb = nbins - 1;
-        bintab[nsq] = static_cast<uint16_t>(tb);
-    }
+    std::vector<uint16_t> bintab;
+    std::vector<int> thresh;
+    t.nsq_max = shell_tables(nbins, umin, umax, bintab, thresh);
     std::vector<double> gfd(ng), ghd(nh), hfd(ng), hhd(nh);
     for (int i = 0; i < ng; ++i) {
         const int ni = i < ng / 2 ? i : i - ng;
@@ -715,17 +708,6 @@ cudaError_t build_spectra_tables(SpectraTables &t, int ng, int order, bool direc
         hhd[i] = sigma_m(w, order) / bhat2(w, order);
         ghd[i] = direct ? hhd[i] : 1.0 / bhat2(w, order);
     }
-    // shell b is the interval thresh[b] <= |n|^2 < thresh[b + 1] (bins are monotone in |n|^2)
-    std::vector<int> thresh(nbins + 1, t.nsq_max + 1);
-    int last = 0;
-    for (int nsq = t.nsq_max; nsq >= 1; --nsq) {
-        const int b = bintab[nsq];
-        if (b == 0xffff) continue;
-        if (!last) last = nsq;
-        for (int k = b; k >= 0 && thresh[k] > nsq; --k) thresh[k] = nsq;
-    }
-    thresh[nbins] = last + 1;
-    for (int k = nbins - 1; k >= 0; --k) thresh[k] = std::min(thresh[k], thresh[k + 1]);
     cudaError_t e;
     if ((e = upload(reinterpret_cast<void **>(&t.bintab), bintab)) != cudaSuccess) return e;
     if ((e = upload(reinterpret_cast<void **>(&t.thresh), thresh)) != cudaSuccess) return e;
@@ -756,16 +738,8 @@ cudaError_t build_spectra_tables(SpectraTables &t, int ng, int order, bool direc
     if ((e = cudaMalloc(reinterpret_cast<void **>(&t.item_partials),
                         static_cast<size_t>(ng) * nbins * kBinVals * sizeof(double))) != cudaSuccess)
         return e;
-    // the non-empty (slab, shell) items (the same test as bin_item's), slabs by increasing
-    // |n0| (0, -1, 1, -2, ...), the outer shells of a slab first
-    std::vector<uint32_t> work;
-    for (int r = 0; r < ng; ++r) {
-        const int k = r >> 1, i0 = (r & 1) ? ng - 1 - k : k;
-        const int n0 = i0 < ng / 2 ? i0 : i0 - ng;
-        for (int b = nbins - 1; b >= 0; --b)
-            if (thresh[b + 1] > thresh[b] && thresh[b + 1] - 1 - n0 * n0 >= 0)
-                work.push_back(static_cast<uint32_t>(i0) * nbins + b);
-    }
+    // the non-empty (slab, shell) items (the same test as bin_item's)
+    std::vector<uint32_t> work = bin_item_list(thresh, ng, nbins);
     t.bin_nwork = static_cast<int>(work.size());
     if (work.empty()) work.push_back(0);  // keep a valid allocation
     if ((e = upload(reinterpret_cast<void **>(&t.bin_order), work)) != cudaSuccess) return e;

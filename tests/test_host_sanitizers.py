@@ -2,6 +2,8 @@
 
 * The oracle's C deposit (oracle/deposit.c) on edge-case positions (0, L, beyond L,
   negative, far outside), orders 1-5 and four fields; field totals conserved.
+* The binning's host-side shell tables and work-item list (csrc/shells.cu, plain C++)
+  against brute force over every mode of small half spectra.
 * The host-side entry points of the C-ABI (include/pkmom.h): defaults, scratch sizes and
   footprints over the parameter ranges, batch work sizes, argument errors, and context
   creation failing cleanly without a GPU. The library's CUDA sources are compiled with
@@ -32,6 +34,18 @@ def test_oracle_deposit_under_sanitizers(tmp_path):
           os.path.join(ROOT, "oracle", "deposit.c"), "-lm"])
     r = _run([exe], env=dict(os.environ, ASAN_OPTIONS="detect_leaks=1", UBSAN_OPTIONS="print_stacktrace=1"))
     assert "deposit ok" in r.stdout
+
+
+def test_shell_tables_and_item_list_under_sanitizers(tmp_path):
+    gxx = shutil.which("g++")
+    if not gxx:
+        pytest.skip("g++ not found")
+    exe = str(tmp_path / "shells_san")
+    csrc = os.path.join(ROOT, "paper_2005_06170_gb300", "csrc")
+    _run([gxx, "-O1", "-std=c++17", *SAN, "-I", csrc, "-o", exe, "-x", "c++", os.path.join(csrc, "shells.cu"),
+          "-x", "c++", os.path.join(HERE, "shells_main.cpp")])
+    r = _run([exe], env=dict(os.environ, ASAN_OPTIONS="detect_leaks=1", UBSAN_OPTIONS="print_stacktrace=1"))
+    assert "shells ok" in r.stdout
 
 
 @pytest.mark.slow
