@@ -255,6 +255,22 @@ def test_ragged_fp32_masses_odd_order(ctx, gpu_lib):
     compare(g, o, 1e-4)
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_more_shells_than_radii(ctx, gpu_lib, prec):
+    """128 shells from k_f to k_N on a 32^3 grid (width 0.12 k_f): the inner shells that
+    no integer |n|^2 reaches are empty (no mode, k NaN), and every (slab, shell) item of
+    the work list is either binned or skipped by the same geometry."""
+    pk = gpu_lib
+    L = 100.0
+    dt = np.float32 if prec == "f32" else np.float64
+    cat = catalogs.poisson(20000, L, seed=61, dtype=dt, bulk=(40.0, -25.0, 10.0))
+    p = pk.params(L, 32, 128, precision=pk.F32 if prec == "f32" else pk.F64)
+    g = run_gpu(ctx, pk, cat, p)
+    o = run_oracle(cat, L, 32, 128)
+    assert (o["n_modes"] == 0).sum() > 10
+    compare(g, o, 1e-4 if prec == "f32" else 1e-9)
+
+
 @pytest.mark.parametrize("order", [1, 2, 4, 5])
 def test_orders_fp64(ctx, gpu_lib, order):
     pk = gpu_lib
